@@ -1,0 +1,220 @@
+/*
+ * gbrng.h -- C ABI of the GB300-native on-the-fly RNG + Langevin-dynamics
+ * library (sm_103a).
+ *
+ * The method is that of Zhmurov, Rybnikov, Kholodov & Barsegov, "Efficient
+ * pseudo-random number generators for biomolecular simulations on graphics
+ * processors": three generators -- Hybrid Taus and Ran2, one generator per
+ * thread (Sec. III.B, Algorithms 1-2), and the additive Lagged Fibonacci
+ * generator shared by all threads (Sec. III.C, Algorithm 3, Table I) --
+ * feeding Box-Muller normals (Sec. II.A) into the Langevin step of N
+ * independent three-dimensional harmonic oscillators (Sec. I and IV).
+ *
+ * Conventions for every entry point:
+ *  - The return value is a gbrng_status; nothing aborts.  On failure
+ *    gbrng_last_error() returns a message (thread-local, valid until the next
+ *    call on the same thread).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  All device work is ordered on that stream.  Calls that return
+ *    host-side results (ld_stats, state blobs, scalar gradients) synchronise
+ *    that stream before returning; the others return after enqueueing.
+ *  - Device pointers passed in (dst, x, v, K_per, dK_per) are owned by the
+ *    caller and must be device-accessible memory of the handle's device.
+ *  - The library owns generator state and scratch.  A handle allocates its
+ *    state in rng_init* and frees everything in rng_destroy.
+ *  - A handle is not thread-safe; calls on one handle must not overlap.
+ *  - Device errors map to GBRNG_ECUDA; a device-side wait that exceeded its
+ *    limit (Lagged Fibonacci chunk flags) maps to GBRNG_ETIMEOUT, after which
+ *    the handle's state is undefined (rng_set_state or a new handle recovers).
+ */
+#ifndef GBRNG_H
+#define GBRNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { GBRNG_TAUS = 0, GBRNG_RAN2 = 1, GBRNG_LAGFIB = 2 } gbrng_kind;
+
+typedef enum {
+    GBRNG_OK = 0,
+    GBRNG_EINVAL = -1,    /* bad argument (null pointer, size, kind, parameter)  */
+    GBRNG_ENOMEM = -2,    /* device or host allocation failed                   */
+    GBRNG_ECUDA = -3,     /* a CUDA runtime call or kernel failed               */
+    GBRNG_ETIMEOUT = -4,  /* a bounded device wait ran out                      */
+    GBRNG_ELAGS = -5,     /* the requested Lagged Fibonacci row cannot be used  */
+    GBRNG_ESTATE = -6     /* a state blob does not match the handle             */
+} gbrng_status;
+
+typedef struct gbrng_rng* gbrng_t;   /* opaque generator handle */
+
+/* ---------------------------------------------------------------- generators */
+
+/* Create a generator of `kind` on the current CUDA device.
+ * Hybrid Taus (Algorithm 1): n_streams independent streams, state 4 x uint32
+ *   per stream (y1, y2, y3 Tausworthe words, y4 LCG word).
+ * Ran2 (Algorithm 2): n_streams independent streams, state 35 x int32 per
+ *   stream (idum, idum2, iy, iv[32]), initialised by the NTAB+8-step warm-up.
+ * Lagged Fibonacci (Algorithm 3): one shared sequence; n_streams is the
+ *   number N of threads (oscillators) per step, which selects the Table I row:
+ *   the smallest row with sl > 4N and ll - sl > 4N, else the last row.
+ * Seeding (Sec. III.B asks for an independent source): word k of stream s is
+ * the low 32 bits of SplitMix64 at counter 8s+k; Taus words 1-3 below 2, 8,
+ * 16 are raised by 2, 8, 16; Ran2 idum = 1 + (word mod (m1-1)); Lagged
+ * Fibonacci seed w (x_{w-ll}) uses counter w, and x_{-ll} is forced odd.
+ * Seeding runs on the GPU.  n_streams >= 1.  *out receives the handle. */
+int rng_init(gbrng_t* out, int kind, uint64_t seed, int64_t n_streams, void* stream);
+
+/* Lagged Fibonacci with an explicit Table I row (0-9, or -1 for the default
+ * row of n_threads).  Row 4 is used as (sl, ll) = (13470, 23209): the printed
+ * sl = 12470 gives a reducible trinomial.  GBRNG_ELAGS for a row outside 0-9. */
+int rng_init_lfg(gbrng_t* out, uint64_t seed, int64_t n_threads, int lag_row, void* stream);
+
+/* Free the handle and everything it owns (waits for its pending work). */
+int rng_destroy(gbrng_t rng);
+
+/* New handle with an identical copy of src's state (device-to-device). */
+int rng_clone(gbrng_t src, gbrng_t* out, void* stream);
+
+/* Query a handle.  Any output pointer may be NULL.  position = number of
+ * Lagged Fibonacci values generated so far (0 for per-thread kinds). */
+int rng_info(gbrng_t rng, int* kind, int64_t* n_streams, int* lag_row, int64_t* position);
+
+/* Table I lags of a row (row 4 as read above).  GBRNG_ELAGS if row not in 0-9. */
+int rng_lfg_lags(int row, int32_t* sl, int32_t* ll);
+
+/* Default Table I row for n_threads (see rng_init). */
+int rng_lfg_default_row(int64_t n_threads);
+
+/* Fill dst_dev[0..n) with raw 32-bit draws.  Per-thread kinds: dst[d*S + s]
+ * is the d-th next draw of stream s (S = n_streams); when S does not divide
+ * n, streams s < n mod S draw once more.  Lagged Fibonacci: dst[k] is the
+ * next value x_{p+k} of the shared sequence.  Ran2 draws are its integer
+ * output iy in [1, m1-1].  n >= 0; the handle advances by the draws made. */
+int rng_fill_u32(gbrng_t rng, uint32_t* dst_dev, int64_t n, void* stream);
+
+/* As rng_fill_u32 with each draw converted to binary32 in [0, 1]:
+ * Taus and Lagged Fibonacci u = fl(raw) * 2^-32 (the multiplier of
+ * Algorithm 1); Ran2 u = min(fl(AM * fl(iy)), RNMX) with AM = fl(1/m1) and
+ * RNMX the largest float below 1 (Algorithm 2). */
+int rng_fill_uniform(gbrng_t rng, float* dst_dev, int64_t n, void* stream);
+
+/* Box-Muller normals, n even.  Pair e = (dst[2e], dst[2e+1]) =
+ * sqrt(-2 ln u1) (cos 2 pi u2, sin 2 pi u2) from two consecutive draws of one
+ * stream; pair e = d*S + s belongs to stream s (Lagged Fibonacci: the values
+ * x_{p+2e}, x_{p+2e+1}).  Taus/Lagged Fibonacci map raw words to the open
+ * interval u = ((raw >> 9) + 1/2) 2^-23; Ran2 uses its uniform.  dst_dev must
+ * be 8-byte aligned (pairs are stored as float2). */
+int rng_fill_normal(gbrng_t rng, float* dst_dev, int64_t n, void* stream);
+
+/* Host blob holding the complete generator state:
+ *   gbrng_state_header, then
+ *   Taus:  uint32 [S][4]   (y1, y2, y3, y4 per stream)
+ *   Ran2:  int32  [S][35]  (idum, idum2, iy, iv[0..31] per stream)
+ *   Lagged Fibonacci: uint32 [ll] = x_{p-ll} .. x_{p-1} in sequence order.
+ * rng_get_state / rng_set_state synchronise the device first and copy with
+ * the legacy default stream.  bytes must equal rng_state_bytes; a blob whose
+ * header does not match the handle gives GBRNG_ESTATE. */
+typedef struct {
+    uint32_t magic;       /* 0x4E524247 ("GBRN") */
+    uint32_t version;     /* 1 */
+    int32_t kind;
+    int32_t lag_row;      /* -1 for per-thread kinds */
+    int64_t n_streams;
+    int64_t position;     /* Lagged Fibonacci p; 0 otherwise */
+    uint64_t payload_bytes;
+} gbrng_state_header;
+
+int rng_state_bytes(gbrng_t rng, size_t* bytes);
+int rng_get_state(gbrng_t rng, void* host, size_t bytes);
+int rng_set_state(gbrng_t rng, const void* host, size_t bytes);
+
+/* Bound (nanoseconds, default 2e9) on every device-side spin wait of the
+ * library (Lagged Fibonacci chunk flags).  A wait that runs out makes the
+ * kernel record GBRNG_ETIMEOUT and return.  Process-wide. */
+int rng_set_wait_limit_ns(uint64_t ns);
+
+/* Test hook for the bounded waits: from the next Lagged Fibonacci launch on,
+ * the CTA that processes launch-relative chunk `chunk` stops publishing its
+ * progress, so every chunk that depends on it waits until the limit runs out
+ * and the call returns GBRNG_ETIMEOUT (no fault, no trap).  -1 switches the
+ * hook off (the default).  Process-wide. */
+int gbrng_test_stall_chunk(int64_t chunk);
+
+/* --------------------------------------------------------- Langevin dynamics */
+
+/* One system of n independent 3-D oscillators (Sec. IV): caller-owned device
+ * arrays x, v of n x 3 binary32 (oscillator-major, x[3i+c]); K_per is a
+ * device array of n spring constants or NULL for the scalar K. */
+typedef struct {
+    int64_t n;
+    float* x;
+    float* v;
+    const float* K_per;
+    double K, m, gamma, kT, dt;
+    gbrng_t rng;          /* per-thread kinds need n_streams >= n */
+} ld_system;
+
+/* Statistics of one run: the final snapshot sums over all oscillators and
+ * components, and the time average over the run's steps of the total energy
+ * E(t) = sum_i (m |v_i(t)|^2 + K_i |x_i(t)|^2) / 2 (states after each step). */
+typedef struct {
+    double sum_x2, sum_v2, sum_xv, energy_time_avg;
+    int64_t steps;
+} ld_stats;
+
+/* Equilibrium start: spends two draw-steps of the generator; step 0 gives
+ * x = sqrt(kT/K_i) g, step 1 gives v = sqrt(kT/m) g (three normals per
+ * oscillator per step as in ld_run). */
+int ld_init_equilibrium(ld_system* sys, void* stream);
+
+/* Advance the system by n_steps of the underdamped Euler-Maruyama step of
+ * m dV/dt = -gamma V - K R + G, G = g sqrt(2 gamma kT dt) (Sec. I):
+ *   v' = (1 - gamma dt/m) v - (dt K_i/m) x + (sqrt(2 gamma kT dt)/m) g,
+ *   x' = x + dt v,
+ * with three Box-Muller normals per oscillator per step drawn from four
+ * uniforms: (g_x, g_y) from (u1, u2), g_z from (u3, u4) (cosine branch).
+ * Per-thread kinds: oscillator i uses stream i.  Lagged Fibonacci: oscillator
+ * j at step t uses sequence positions p0 + 4(j + N t) + r, r = 0..3.
+ * binary32 arithmetic order (exact, no contraction):
+ *   coefficients (double, rounded once): cdt = dt, cva = 1 - (gamma dt)/m,
+ *   ckm = dt/m, cs = sqrt(2 gamma kT dt)/m;  ckx = ckm * K_i;
+ *   per component: t = fma(-ckx, x, cs * g); v' = fma(cva, v, t);
+ *   x' = fma(cdt, v, x).
+ * out_host (nullable) receives the run's statistics (synchronises stream).
+ * Requirements: n >= 0, n_steps >= 0, m > 0, dt > 0, gamma >= 0, kT >= 0,
+ * K > 0 (or K_per given). */
+int ld_run(ld_system* sys, int64_t n_steps, ld_stats* out_host, void* stream);
+
+/* Run n_sys independent systems (own handle, parameters and arrays each;
+ * per-thread kinds only) as one persistent launch per steps-per-launch chunk,
+ * captured once into a CUDA graph.  tune = {threads per block, oscillators
+ * per thread, steps per launch} or NULL to autotune (results cached per shape
+ * in the file named by $GBRNG_TUNE_CACHE, if set).  Trajectories and
+ * generator states equal those of one ld_run per system bit for bit.
+ * out (nullable) receives n_sys stats (synchronises stream). */
+int ld_run_batched(ld_system* sys, int n_sys, int64_t n_steps, const int* tune,
+                   ld_stats* out, void* stream);
+
+/* Reverse-time adjoint of L = (1/S) sum_{t=1..S} E(t) (S = n_steps) under the
+ * fixed noise of the generator, starting from the system's current state.
+ * Generator states and (x, v) are checkpointed every ckpt_every steps; the
+ * noise of each segment is regenerated bit-exactly for its reverse sweep.
+ * Leaves the system advanced exactly as ld_run(sys, n_steps) would.
+ * dK_per (device [n], nullable) receives dL/dK_i; *dgamma, *dkT (nullable)
+ * receive dL/dgamma, dL/dkT; *loss (nullable) receives L.  Per-thread kinds
+ * only; requires gamma > 0, kT > 0, n_steps >= 1, ckpt_every >= 1.
+ * Synchronises stream. */
+int ld_backward(ld_system* sys, int64_t n_steps, int ckpt_every, float* dK_per,
+                double* dgamma, double* dkT, double* loss, void* stream);
+
+/* ----------------------------------------------------------------- errors */
+const char* gbrng_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GBRNG_H */

@@ -1,0 +1,194 @@
+// Device-side building blocks: the three generators, conversions,
+// Box-Muller, the Euler-Maruyama step and deterministic reductions.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace gb {
+
+// ------------------------------------------------------------------ seeding
+// SplitMix64 (Steele, Lea & Flood 2014) evaluated at counter idx.
+__host__ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t idx)
+{
+    uint64_t z = seed + (idx + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// ------------------------------------------------------------- Hybrid Taus
+// One Tausworthe word step (Algorithm 1): b = ((y << S1) ^ y) >> S2,
+// y = ((y & C) << S3) ^ b.
+template <int S1, int S2, int S3, uint32_t C>
+__device__ __forceinline__ uint32_t taus_word(uint32_t y)
+{
+    const uint32_t b = ((y << S1) ^ y) >> S2;
+    return ((y & C) << S3) ^ b;
+}
+
+// Advance the three Tausworthe words and the LCG, return their xor.
+__device__ __forceinline__ uint32_t taus_next(uint4& s)
+{
+    s.x = taus_word<13, 19, 12, 0xFFFFFFFEu>(s.x);
+    s.y = taus_word<2, 25, 4, 0xFFFFFFF8u>(s.y);
+    s.z = taus_word<3, 11, 17, 0xFFFFFFF0u>(s.z);
+    s.w = 1664525u * s.w + 1013904223u;
+    return s.x ^ s.y ^ s.z ^ s.w;
+}
+
+// -------------------------------------------------------------------- Ran2
+// L'Ecuyer's pair (m1, a1) = (2147483563, 40014), (m2, a2) = (2147483399,
+// 40692) with Schrage's q = m div a, r = m mod a; 32-entry shuffle table.
+constexpr int32_t kR2M1 = 2147483563, kR2A1 = 40014, kR2Q1 = 53668, kR2R1 = 12211;
+constexpr int32_t kR2M2 = 2147483399, kR2A2 = 40692, kR2Q2 = 52774, kR2R2 = 3791;
+constexpr int32_t kR2Imm1 = kR2M1 - 1;
+constexpr int32_t kR2Ndiv = 1 + kR2Imm1 / 32;
+static_assert(kR2Q1 == kR2M1 / kR2A1 && kR2R1 == kR2M1 % kR2A1, "Schrage constants");
+static_assert(kR2Q2 == kR2M2 / kR2A2 && kR2R2 == kR2M2 % kR2A2, "Schrage constants");
+
+// a*x mod m for 0 < x < m (Algorithm 2, lines 21-28).  x is positive, so the
+// quotient uses unsigned division by a constant (a multiply-high).
+template <int32_t A, int32_t M, int32_t Q, int32_t R>
+__host__ __device__ __forceinline__ int32_t schrage(int32_t x)
+{
+    const int32_t k = (int32_t)((uint32_t)x / (uint32_t)Q);
+    int32_t y = A * (x - k * Q) - k * R;
+    return y < 0 ? y + M : y;
+}
+
+// One Ran2 draw; the shuffle table is addressed through `iv(j)` so that it can
+// live in shared memory ([32][threads]) or global memory.
+struct Ran2Regs {
+    int32_t idum, idum2, iy;
+};
+
+template <class TableRef>
+__device__ __forceinline__ int32_t ran2_next(Ran2Regs& r, TableRef iv)
+{
+    r.idum = schrage<kR2A1, kR2M1, kR2Q1, kR2R1>(r.idum);
+    r.idum2 = schrage<kR2A2, kR2M2, kR2Q2, kR2R2>(r.idum2);
+    const int j = (int)((uint32_t)r.iy / (uint32_t)kR2Ndiv);   // previous iy
+    int32_t y = iv(j) - r.idum2;
+    iv(j) = r.idum;
+    if (y < 1) y += kR2Imm1;
+    r.iy = y;
+    return y;
+}
+
+// ------------------------------------------------------------- conversions
+// Taus / Lagged Fibonacci uniform: fl(raw) * 2^-32 in [0, 1].
+__device__ __forceinline__ float u01_from_u32(uint32_t raw)
+{
+    return __fmul_rn(__uint2float_rn(raw), 0x1p-32f);
+}
+
+// Ran2 uniform: min(fl(AM * fl(iy)), RNMX), AM = fl(1/m1), RNMX < 1.
+__device__ __forceinline__ float u01_from_ran2(int32_t iy)
+{
+    const float am = 0x1p-31f;   // fl32(1/2147483563) rounds to 2^-31 exactly
+    const float rnmx = 0x1.fffffep-1f;
+    return fminf(__fmul_rn(am, __int2float_rn(iy)), rnmx);
+}
+
+// Open-interval Box-Muller input ((raw >> 9) + 1/2) * 2^-23: the 24-bit odd
+// integer (raw >> 8) | 1 scaled by 2^-24, exact in binary32.
+__device__ __forceinline__ float open01_from_u32(uint32_t raw)
+{
+    return __fmul_rn(__uint2float_rn((raw >> 8) | 1u), 0x1p-24f);
+}
+
+// Box-Muller pair from two uniforms in (0, 1).
+__device__ __forceinline__ void box_muller(float u1, float u2, float& g1, float& g2)
+{
+    const float rho = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    g1 = __fmul_rn(rho, c);
+    g2 = __fmul_rn(rho, s);
+}
+
+// Only the cosine branch (third normal of a particle-step).
+__device__ __forceinline__ float box_muller_cos(float u1, float u2)
+{
+    const float rho = sqrtf(-2.0f * logf(u1));
+    return __fmul_rn(rho, cospif(2.0f * u2));
+}
+
+// ------------------------------------------------------------------ LD step
+// v' = fma(cva, v, fma(-ckx, x, cs * g)),  x' = fma(cdt, v, x).
+__device__ __forceinline__ void em_component(float cdt, float cva, float ckx, float cs, float g,
+                                             float& x, float& v)
+{
+    const float t = __fmaf_rn(-ckx, x, __fmul_rn(cs, g));
+    const float vn = __fmaf_rn(cva, v, t);
+    x = __fmaf_rn(cdt, v, x);
+    v = vn;
+}
+
+// Kahan-compensated binary32 accumulator.
+struct Kahan {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float e)
+    {
+        const float y = __fsub_rn(e, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Deterministic block reduction of N doubles per thread (fixed tree order);
+// thread 0 receives the block totals in `v`.  smem must hold N*32 doubles.
+template <int N>
+__device__ __forceinline__ void block_reduce_sum(double (&v)[N], double* smem)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < N; ++k) smem[k * 32 + warp] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            v[k] = lane < nwarps ? smem[k * 32 + lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+        }
+    }
+    __syncthreads();
+}
+
+// Cheap global-timer read for bounded waits.
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int* p)
+{
+    return *(const volatile int*)p;
+}
+
+}  // namespace gb

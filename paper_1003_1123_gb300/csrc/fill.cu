@@ -1,0 +1,128 @@
+// Stand-alone fills for the per-thread generators (Hybrid Taus, Ran2):
+// out[d*S + s] is the d-th draw of stream s.  One thread owns one stream at a
+// time and keeps its state in registers (Taus) or in a shared-memory column
+// (Ran2's shuffle table) for all of its draws; stores are coalesced across
+// the streams of a warp.
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace gb {
+
+enum { FILL_U32 = 0, FILL_UNIFORM = 1, FILL_NORMAL = 2 };
+
+template <int MODE>
+__device__ __forceinline__ void emit_taus(uint4& y, int64_t idx, void* out)
+{
+    if (MODE == FILL_U32) {
+        ((uint32_t*)out)[idx] = taus_next(y);
+    } else if (MODE == FILL_UNIFORM) {
+        ((float*)out)[idx] = u01_from_u32(taus_next(y));
+    } else {
+        const float u1 = open01_from_u32(taus_next(y));
+        const float u2 = open01_from_u32(taus_next(y));
+        float2 g;
+        box_muller(u1, u2, g.x, g.y);
+        ((float2*)out)[idx] = g;
+    }
+}
+
+// n_items = numbers (u32, uniform) or pairs (normal).
+template <int MODE>
+__global__ void __launch_bounds__(256) taus_fill_kernel(uint4* __restrict__ st, int64_t S,
+                                                        int64_t n_items, void* __restrict__ out)
+{
+    const int64_t active = S < n_items ? S : n_items;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < active; s += stride) {
+        uint4 y = st[s];
+        int64_t idx = s;
+        // four draws in flight per iteration: independent stores, one state chain
+        for (; idx + 3 * S < n_items; idx += 4 * S) {
+            emit_taus<MODE>(y, idx, out);
+            emit_taus<MODE>(y, idx + S, out);
+            emit_taus<MODE>(y, idx + 2 * S, out);
+            emit_taus<MODE>(y, idx + 3 * S, out);
+        }
+        for (; idx < n_items; idx += S) emit_taus<MODE>(y, idx, out);
+        st[s] = y;
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) ran2_fill_kernel(int32_t* __restrict__ st, int64_t S,
+                                                        int64_t n_items, void* __restrict__ out)
+{
+    extern __shared__ int32_t tab[];      // [32][blockDim.x]
+    const int T = blockDim.x, tid = threadIdx.x;
+    auto iv = [&](int j) -> int32_t& { return tab[j * T + tid]; };
+    const int64_t active = S < n_items ? S : n_items;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + tid; s < active; s += stride) {
+        Ran2Regs r{st[s], st[S + s], st[2 * S + s]};
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) iv(j) = st[(3 + j) * S + s];
+        for (int64_t idx = s; idx < n_items; idx += S) {
+            if (MODE == FILL_U32) {
+                ((uint32_t*)out)[idx] = (uint32_t)ran2_next(r, iv);
+            } else if (MODE == FILL_UNIFORM) {
+                ((float*)out)[idx] = u01_from_ran2(ran2_next(r, iv));
+            } else {
+                const float u1 = u01_from_ran2(ran2_next(r, iv));
+                const float u2 = u01_from_ran2(ran2_next(r, iv));
+                float2 g;
+                box_muller(u1, u2, g.x, g.y);
+                ((float2*)out)[idx] = g;
+            }
+        }
+        st[s] = r.idum;
+        st[S + s] = r.idum2;
+        st[2 * S + s] = r.iy;
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) st[(3 + j) * S + s] = iv(j);
+    }
+}
+
+template <int MODE>
+static int fill_pt(Handle* h, void* dst, int64_t n_items, cudaStream_t st)
+{
+    DevInfo di;
+    GB_CHECK(dev_info(h->device, &di));
+    const int64_t active = h->n < n_items ? h->n : n_items;
+    if (h->kind == GBRNG_TAUS) {
+        const int T = 256;
+        int occ = 0;
+        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, taus_fill_kernel<MODE>, T, 0));
+        int64_t blocks = (active + T - 1) / T;
+        const int64_t cap = (int64_t)di.sms * (occ > 0 ? occ : 1);
+        if (blocks > cap) blocks = cap;
+        taus_fill_kernel<MODE><<<(unsigned)blocks, T, 0, st>>>(h->taus, h->n, n_items, dst);
+    } else {
+        const int T = 128;
+        const size_t smem = sizeof(int32_t) * 32 * T;
+        int occ = 0;
+        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ran2_fill_kernel<MODE>, T, smem));
+        int64_t blocks = (active + T - 1) / T;
+        const int64_t cap = (int64_t)di.sms * (occ > 0 ? occ : 1);
+        if (blocks > cap) blocks = cap;
+        ran2_fill_kernel<MODE><<<(unsigned)blocks, T, smem, st>>>(h->r2, h->n, n_items, dst);
+    }
+    GB_CUDA(cudaGetLastError());
+    return GBRNG_OK;
+}
+
+int fill_u32_pt(Handle* h, uint32_t* dst, int64_t n, cudaStream_t st)
+{
+    return fill_pt<FILL_U32>(h, dst, n, st);
+}
+
+int fill_uniform_pt(Handle* h, float* dst, int64_t n, cudaStream_t st)
+{
+    return fill_pt<FILL_UNIFORM>(h, dst, n, st);
+}
+
+int fill_normal_pt(Handle* h, float* dst, int64_t n, cudaStream_t st)
+{
+    return fill_pt<FILL_NORMAL>(h, dst, n / 2, st);
+}
+
+}  // namespace gb

@@ -1,0 +1,196 @@
+// Fused Langevin dynamics for the per-thread generators (Hybrid Taus, Ran2):
+// one persistent launch runs every step of every oscillator.  A thread owns
+// oscillators i = g, g + W, g + 2W, ... (W = threads in the grid) and, for
+// each, keeps x, v, K_i and the generator state in registers (Ran2's shuffle
+// table in a shared-memory column) for all n_steps; per step it draws four
+// uniforms, forms three Box-Muller normals, applies the Euler-Maruyama update
+// and accumulates the energy.  State goes back to global memory once.
+#include "device.cuh"
+#include "internal.cuh"
+
+namespace gb {
+
+struct LdArgs {
+    int64_t n, n_steps;
+    float* x;
+    float* v;
+    const float* Kper;
+    LdCoef c;
+    uint4* taus;       // Taus state [streams]
+    int32_t* r2;       // Ran2 state [35][streams]
+    int64_t S;         // streams of the generator (row stride of r2)
+    double* partials;  // [gridDim.x][4]
+};
+
+// Three normals of one particle-step from four draws of the generator.
+struct TausDraw {
+    uint4 y;
+    __device__ __forceinline__ void normals3(float& gx, float& gy, float& gz)
+    {
+        const float u1 = open01_from_u32(taus_next(y));
+        const float u2 = open01_from_u32(taus_next(y));
+        const float u3 = open01_from_u32(taus_next(y));
+        const float u4 = open01_from_u32(taus_next(y));
+        box_muller(u1, u2, gx, gy);
+        gz = box_muller_cos(u3, u4);
+    }
+};
+
+struct Ran2Draw {
+    Ran2Regs r;
+    int32_t* tab;
+    int T, tid;
+    __device__ __forceinline__ int32_t next()
+    {
+        int32_t* t = tab;
+        const int TT = T, ti = tid;
+        return ran2_next(r, [t, TT, ti](int j) -> int32_t& { return t[j * TT + ti]; });
+    }
+    __device__ __forceinline__ void normals3(float& gx, float& gy, float& gz)
+    {
+        const float u1 = u01_from_ran2(next());
+        const float u2 = u01_from_ran2(next());
+        const float u3 = u01_from_ran2(next());
+        const float u4 = u01_from_ran2(next());
+        box_muller(u1, u2, gx, gy);
+        gz = box_muller_cos(u3, u4);
+    }
+};
+
+template <int KIND, bool INIT>
+__global__ void __launch_bounds__(128) ld_pt_kernel(LdArgs a)
+{
+    extern __shared__ int32_t tab[];   // Ran2: [32][blockDim.x]
+    __shared__ double red[4 * 32];
+    const int64_t W = (int64_t)gridDim.x * blockDim.x;
+    const LdCoef c = a.c;
+    double acc[4] = {0, 0, 0, 0};      // sum x^2, v^2, x.v, energy
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n; i += W) {
+        const float Ki = a.Kper ? a.Kper[i] : c.K;
+        float x0, x1, x2, v0, v1, v2;
+        if (!INIT) {
+            x0 = a.x[3 * i], x1 = a.x[3 * i + 1], x2 = a.x[3 * i + 2];
+            v0 = a.v[3 * i], v1 = a.v[3 * i + 1], v2 = a.v[3 * i + 2];
+        }
+        TausDraw td;
+        Ran2Draw rd;
+        if (KIND == GBRNG_TAUS) {
+            td.y = a.taus[i];
+        } else {
+            rd.tab = tab;
+            rd.T = blockDim.x;
+            rd.tid = threadIdx.x;
+            rd.r.idum = a.r2[i];
+            rd.r.idum2 = a.r2[a.S + i];
+            rd.r.iy = a.r2[2 * a.S + i];
+#pragma unroll 4
+            for (int j = 0; j < 32; ++j) tab[j * blockDim.x + threadIdx.x] = a.r2[(3 + j) * a.S + i];
+        }
+        Kahan e;
+        if (INIT) {
+            // draw-step 0 -> x = sqrt(kT/K_i) g, draw-step 1 -> v = sqrt(kT/m) g
+            float g0, g1, g2;
+            if (KIND == GBRNG_TAUS) td.normals3(g0, g1, g2); else rd.normals3(g0, g1, g2);
+            const float sx = __fsqrt_rn(__fdiv_rn(c.kT, Ki));
+            x0 = __fmul_rn(sx, g0), x1 = __fmul_rn(sx, g1), x2 = __fmul_rn(sx, g2);
+            if (KIND == GBRNG_TAUS) td.normals3(g0, g1, g2); else rd.normals3(g0, g1, g2);
+            v0 = __fmul_rn(c.sv, g0), v1 = __fmul_rn(c.sv, g1), v2 = __fmul_rn(c.sv, g2);
+        } else {
+            const float ckx = __fmul_rn(c.ckm, Ki);
+            const float hK = 0.5f * Ki;
+            for (int64_t t = 0; t < a.n_steps; ++t) {
+                float g0, g1, g2;
+                if (KIND == GBRNG_TAUS) td.normals3(g0, g1, g2); else rd.normals3(g0, g1, g2);
+                em_component(c.cdt, c.cva, ckx, c.cs, g0, x0, v0);
+                em_component(c.cdt, c.cva, ckx, c.cs, g1, x1, v1);
+                em_component(c.cdt, c.cva, ckx, c.cs, g2, x2, v2);
+                const float xx = x0 * x0 + x1 * x1 + x2 * x2;
+                const float vv = v0 * v0 + v1 * v1 + v2 * v2;
+                e.add(hK * xx + c.hm * vv);
+            }
+        }
+        a.x[3 * i] = x0, a.x[3 * i + 1] = x1, a.x[3 * i + 2] = x2;
+        a.v[3 * i] = v0, a.v[3 * i + 1] = v1, a.v[3 * i + 2] = v2;
+        if (KIND == GBRNG_TAUS) {
+            a.taus[i] = td.y;
+        } else {
+            a.r2[i] = rd.r.idum;
+            a.r2[a.S + i] = rd.r.idum2;
+            a.r2[2 * a.S + i] = rd.r.iy;
+#pragma unroll 4
+            for (int j = 0; j < 32; ++j) a.r2[(3 + j) * a.S + i] = tab[j * blockDim.x + threadIdx.x];
+        }
+        acc[0] += (double)x0 * x0 + (double)x1 * x1 + (double)x2 * x2;
+        acc[1] += (double)v0 * v0 + (double)v1 * v1 + (double)v2 * v2;
+        acc[2] += (double)x0 * v0 + (double)x1 * v1 + (double)x2 * v2;
+        acc[3] += e.value();
+    }
+    if (a.partials) {
+        block_reduce_sum<4>(acc, red);
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) a.partials[4 * blockIdx.x + k] = acc[k];
+    }
+}
+
+// Grid shape: threads per block T, then the fewest oscillators per thread
+// that fit one resident wave, then as many blocks as needed for that count;
+// every SM receives about the same number of oscillators.
+template <int KIND, bool INIT>
+static int launch_ld(const ld_system* s, int64_t n_steps, bool want_stats, int64_t* blocks_out,
+                     cudaStream_t st)
+{
+    Handle* h = s->rng;
+    DevInfo di;
+    GB_CHECK(dev_info(h->device, &di));
+    int T = 128;
+    if (s->n < (int64_t)di.sms * 128 * 2) T = 32;   // spread small systems over all SMs
+    const size_t smem = KIND == GBRNG_RAN2 ? sizeof(int32_t) * 32 * T : 0;
+    int occ = 0;
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ld_pt_kernel<KIND, INIT>, T, smem));
+    if (occ < 1) occ = 1;
+    const int64_t wave = (int64_t)di.sms * occ * T;
+    const int64_t per_thread = (s->n + wave - 1) / wave;
+    int64_t blocks = (s->n + per_thread * T - 1) / (per_thread * T);
+    if (blocks < 1) blocks = 1;
+    if (want_stats) GB_CHECK(ensure_partials(h, blocks));
+    LdArgs a;
+    a.n = s->n;
+    a.n_steps = n_steps;
+    a.x = s->x;
+    a.v = s->v;
+    a.Kper = s->K_per;
+    a.c = make_coef(s);
+    a.taus = h->taus;
+    a.r2 = h->r2;
+    a.S = h->n;
+    a.partials = want_stats ? h->partials : nullptr;
+    ld_pt_kernel<KIND, INIT><<<(unsigned)blocks, T, smem, st>>>(a);
+    GB_CUDA(cudaGetLastError());
+    *blocks_out = blocks;
+    return GBRNG_OK;
+}
+
+int ld_init_pt(const ld_system* s, cudaStream_t st)
+{
+    int64_t blocks = 0;
+    if (s->rng->kind == GBRNG_TAUS) return launch_ld<GBRNG_TAUS, true>(s, 0, false, &blocks, st);
+    return launch_ld<GBRNG_RAN2, true>(s, 0, false, &blocks, st);
+}
+
+int ld_run_pt(const ld_system* s, int64_t n_steps, ld_stats* out, cudaStream_t st)
+{
+    if (s->n == 0) {
+        if (out) *out = ld_stats{0, 0, 0, 0, n_steps};
+        return GBRNG_OK;
+    }
+    int64_t blocks = 0;
+    const bool want = out != nullptr;
+    if (s->rng->kind == GBRNG_TAUS)
+        GB_CHECK((launch_ld<GBRNG_TAUS, false>(s, n_steps, want, &blocks, st)));
+    else
+        GB_CHECK((launch_ld<GBRNG_RAN2, false>(s, n_steps, want, &blocks, st)));
+    return finish_stats(s->rng, blocks, n_steps, out, st);
+}
+
+}  // namespace gb

@@ -1,0 +1,181 @@
+"""GPU parity of the three generators against the CPU oracle, through the C
+ABI: raw streams bit-exact, uniforms bit-exact, Box-Muller normals within the
+transcendental tolerance, states and run splitting exact."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1003_1123_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# Box-Muller normals: CUDA's logf / sincospif are within 1 ulp, sqrtf is
+# correctly rounded; the oracle rounds rho, cos and sin once each from double.
+# Both sides are within ~2.5 ulp of the exact value: |d| <= 4 ulp(g).
+NORMAL_RTOL, NORMAL_ATOL = 2e-6, 1e-7
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1003_1123_gb300 import gbrng
+    gbrng.lib()
+    return gbrng
+
+
+def u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+def state_payload(G, rng):
+    hd, payload = G.parse_state(G.rng_get_state(rng))
+    return hd, payload
+
+
+def oracle_state_bytes(g):
+    if g.kind == oracle.LAGFIB:
+        return g.ring_in_order().tobytes()
+    return g.state.tobytes()
+
+
+KINDS = ["taus", "ran2", "lagfib"]
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_seeding_matches_oracle(G, kind):
+    """rng_init seeds on the GPU exactly as the oracle seeds on the CPU."""
+    n = 1000
+    r = G.rng_init(kind, 42, n)
+    g = oracle.Gen(kind, 42, n)
+    hd, payload = state_payload(G, r)
+    assert hd["kind"] == g.kind and hd["n_streams"] == n
+    assert payload == oracle_state_bytes(g)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_raw_stream_small_config_bit_exact(G, kind):
+    """Seed 1234, 4096 streams (threads), 2^20 raw numbers: bit-exact, and the
+    generator state afterwards equals the oracle's."""
+    c = W.SMALL
+    r = G.rng_init(kind, c["seed"], c["n"])
+    g = oracle.Gen(kind, c["seed"], c["n"])
+    got = u32(G.rng_fill_u32(r, c["raw_n"]))
+    exp = g.fill_u32(c["raw_n"])
+    assert np.array_equal(got, exp)
+    assert state_payload(G, r)[1] == oracle_state_bytes(g)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("n", [0, 1, 7, 4096 * 3 + 17, 100003])
+def test_raw_stream_ragged_sizes(G, kind, n):
+    """Sizes that are not a multiple of the streams or the chunk; two calls in
+    a row continue the streams."""
+    S = 333
+    r = G.rng_init(kind, 5, S)
+    g = oracle.Gen(kind, 5, S)
+    for _ in range(2):
+        got = u32(G.rng_fill_u32(r, n)) if n else np.zeros(0, np.uint32)
+        assert np.array_equal(got, g.fill_u32(n))
+    assert state_payload(G, r)[1] == oracle_state_bytes(g)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_uniform_bit_exact(G, kind):
+    r = G.rng_init(kind, 9, 2048)
+    g = oracle.Gen(kind, 9, 2048)
+    got = G.rng_fill_uniform(r, 300001).cpu().numpy()
+    exp = g.fill_uniform(300001)
+    assert np.array_equal(got.view(np.uint32), exp.view(np.uint32))
+    assert got.min() >= 0.0 and got.max() <= 1.0
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_normal_within_tolerance(G, kind):
+    r = G.rng_init(kind, 11, 2048)
+    g = oracle.Gen(kind, 11, 2048)
+    n = 2 * 150001
+    got = G.rng_fill_normal(r, n).cpu().numpy().astype(np.float64)
+    exp = g.fill_normal(n).astype(np.float64)
+    err = np.abs(got - exp)
+    assert (err <= NORMAL_RTOL * np.abs(exp) + NORMAL_ATOL).all(), err.max()
+    assert state_payload(G, r)[1] == oracle_state_bytes(g)
+
+
+@pytest.mark.parametrize("row", list(range(10)))
+def test_lfg_every_table_row(G, row):
+    """Every Table I row: several dependency rounds (n >> ll - sl), odd split."""
+    sl, ll = oracle.lfg_table(row)
+    n = min(3 * ll + 12345, 4 * 10**6)
+    r = G.rng_init_lfg(3, 100, row)
+    g = oracle.Gen("lagfib", 3, 100, lag_row=row)
+    a = n // 3 + 1
+    got = np.concatenate([u32(G.rng_fill_u32(r, a)), u32(G.rng_fill_u32(r, n - a))])
+    assert np.array_equal(got, g.fill_u32(n))
+    assert G.rng_info(r)["position"] == n
+    assert state_payload(G, r)[1] == oracle_state_bytes(g)
+
+
+def test_lfg_full_size_fill_bit_exact(G):
+    """2^30 values of the last Table I row, compared in full (the oracle runs
+    the serial recurrence chunk by chunk beside the GPU copy)."""
+    n, chunk = 2**30, 2**26
+    r = G.rng_init("lagfib", 2024, 10**6)
+    out = G.rng_fill_u32(r, n)
+    g = oracle.Gen("lagfib", 2024, 10**6)
+    assert g.lags == (1010202, 3021377)
+    for k in range(0, n, chunk):
+        assert np.array_equal(u32(out[k:k + chunk]), g.fill_u32(chunk)), k
+    assert state_payload(G, r)[1] == oracle_state_bytes(g)
+
+
+@pytest.mark.parametrize("kind", ["taus", "ran2"])
+def test_per_thread_full_size_fill_sampled(G, kind):
+    """2^30 numbers from 10^6 streams: every output of 64 sampled streams is
+    compared with the oracle running just those streams."""
+    S, n = 10**6, 2**30
+    r = G.rng_init(kind, 2024, S)
+    out = G.rng_fill_uniform(r, n)
+    g = oracle.Gen(kind, 2024, S)
+    picks = np.unique(np.concatenate([[0, 1, S - 1, n % S - 1, n % S],
+                                      np.random.default_rng(0).integers(0, S, 59)]))
+    for s in picks:
+        sub = oracle.Gen(kind, 2024, 1)
+        sub.state[:] = g.state[s]
+        cnt = (n - s + S - 1) // S
+        exp = sub.fill_uniform(cnt)
+        idx = torch.arange(cnt, device="cuda", dtype=torch.int64) * S + int(s)
+        got = out[idx].cpu().numpy()
+        assert np.array_equal(got.view(np.uint32), exp.view(np.uint32)), s
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_state_roundtrip_and_clone(G, kind):
+    """get_state / set_state and rng_clone continue the stream exactly."""
+    r = G.rng_init(kind, 77, 500)
+    G.rng_fill_u32(r, 12345)
+    blob = G.rng_get_state(r)
+    c = G.rng_clone(r)
+    a = u32(G.rng_fill_u32(r, 54321))
+    b = u32(G.rng_fill_u32(c, 54321))
+    G.rng_set_state(r, blob)
+    d = u32(G.rng_fill_u32(r, 54321))
+    assert np.array_equal(a, b) and np.array_equal(a, d)
+    bad = bytearray(blob)
+    bad[0] ^= 1
+    with pytest.raises(G.GbrngError) as e:
+        G.rng_set_state(r, bytes(bad))
+    assert e.value.code == -6
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_large_normal_moments(G, kind):
+    """Box-Muller normals at 2^26: mean 0, variance 1, kurtosis 3 (5 sigma)."""
+    r = G.rng_init(kind, 123, 10**6 if kind != "lagfib" else 10**6)
+    z = G.rng_fill_normal(r, 2**26).double()
+    n = z.numel()
+    m, var = z.mean().item(), z.var().item()
+    k = (((z - m) ** 4).mean() / var**2).item()
+    assert abs(m) < 5 / n**0.5 and abs(var - 1) < 5 * (2 / n) ** 0.5
+    assert abs(k - 3) < 5 * (24 / n) ** 0.5
