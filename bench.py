@@ -1,0 +1,476 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the on-the-fly RNG + Langevin-dynamics hot path.
+
+One bench step is one pass of the whole hot path over the throughput
+workload (10^6 independent 3-D oscillators, the paper's Sec. IV test shape):
+  - fused Langevin dynamics, 10^4 steps, for each generator (Hybrid Taus,
+    Ran2, Lagged Fibonacci on the last Table I row), seeding excluded;
+  - stand-alone fills of 2^30 uniform and 2^30 normal binary32 numbers per
+    generator;
+  - the batched and adjoint paths when the library provides them.
+value = oscillator-steps advanced per second over the whole step (fills
+count toward the time, not the oscillator-steps).  Inputs stay resident in
+HBM; the L2 (126 MB) is flushed by a 256 MiB write before every timed part.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbrng|reference]
+
+With --impl reference the CPU oracle is timed on bounded samples of the same
+workload on this machine's host cores (oracle/ is test infrastructure; only
+that leg and the cpu_baseline leg run it).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_OSC = 10**6
+LD_STEPS = 10**4
+FILL_N = 2**30
+SEED = 2024
+KINDS = ("taus", "ran2", "lagfib")
+L2_FLUSH_BYTES = 256 << 20
+PARAMS = dict(K=1.0, m=1.0, gamma=0.5, kT=1.0, dt=0.01)
+
+# Integer operations per oscillator-step that the generators themselves
+# require (four draws): Hybrid Taus 4 x (3 x 5 shift/logic + 1 LCG multiply-
+# add + 2 combining xors) = 72; Ran2 4 x (2 Schrage steps of 5 (multiply-high
+# quotient, two multiply-adds, compare-add) + table index, subtract, wrap) = 52.
+INT_OPS_PER_OSC_STEP = {"taus": 72, "ran2": 52}
+# Algorithmic bytes per oscillator-step of the Lagged Fibonacci fused step:
+# four ring values (2 lag reads + 1 write each, 4 B) = 48 B, plus x, v read and
+# written (24 + 24 B) = 96 B.
+LFG_BYTES_PER_OSC_STEP = 96
+FILL_BYTES_PER_NUMBER = 4
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# Peak integer-ALU rate: 152 SMs x 64 INT32 lanes per SM (four partitions of 16)
+# x SM clock.  The lane count was measured with an issue-rate microbenchmark
+# (see the design doc); the clock is the median sampled during the timed region.
+SMS = 152
+INT32_LANES_PER_SM = 64
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during timing."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        mhz = [int(r[1]) for r in rows]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": int(rows[0][2]),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------- GPU
+class Workload:
+    def __init__(self, G, torch, rank: int):
+        self.G, self.torch = G, torch
+        seed = SEED + 1000003 * rank
+        self.systems = {}
+        for kind in KINDS:
+            r = G.rng_init(kind, seed, N_OSC)
+            x = torch.zeros((N_OSC, 3), dtype=torch.float32, device="cuda")
+            v = torch.zeros_like(x)
+            s = G.LdSystem(r, x, v, **PARAMS)
+            G.ld_init_equilibrium(s)
+            self.systems[kind] = s
+        self.fill_rngs = {k: G.rng_init(k, seed + 7, N_OSC) for k in KINDS}
+        self.out = torch.empty(FILL_N, dtype=torch.float32, device="cuda")
+        self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+
+    def parts(self):
+        G = self.G
+        out = []
+        for kind in KINDS:
+            s = self.systems[kind]
+            out.append((f"ld_{kind}", N_OSC * LD_STEPS, lambda s=s: G.ld_run(s, LD_STEPS)))
+        for kind in KINDS:
+            r = self.fill_rngs[kind]
+            out.append((f"fill_uniform_{kind}", 0,
+                        lambda r=r: G.rng_fill_uniform(r, FILL_N, out=self.out)))
+            out.append((f"fill_normal_{kind}", 0,
+                        lambda r=r: G.rng_fill_normal(r, FILL_N, out=self.out)))
+        return out
+
+    def step(self, parts, events):
+        for i, (_, _, fn) in enumerate(parts):
+            self.flush.fill_(float(i))
+            events[i][0].record()
+            fn()
+            events[i][1].record()
+
+
+def run_gpu(args, rank, world, dist):
+    import torch
+    from paper_1003_1123_gb300 import gbrng as G
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    wl = Workload(G, torch, rank)
+    parts = wl.parts()
+    osc_steps_per_step = sum(p[1] for p in parts)
+    ev = [[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+          for _ in parts]
+    for _ in range(args.warmup):
+        wl.step(parts, ev)
+    torch.cuda.synchronize()
+
+    part_ms = {name: 0.0 for name, _, _ in parts}
+    clocks = Clocks(dev)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record()
+    for _ in range(args.steps):
+        wl.step(parts, ev)
+        torch.cuda.synchronize()
+        for i, (name, _, _) in enumerate(parts):
+            part_ms[name] += ev[i][0].elapsed_time(ev[i][1])
+    t_end.record()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    ms_per_step = elapsed_ms / args.steps
+    value = world * osc_steps_per_step / (ms_per_step / 1e3)
+
+    # ---- end to end through host buffers (pinned inputs and outputs)
+    e2e = run_e2e(args, wl, parts, G, torch)
+
+    # ---- roofline of the dominant part
+    peaks, peak_src = load_peaks()
+    dom = max(part_ms, key=part_ms.get)
+    dom_ms = part_ms[dom] / args.steps
+    roof = roofline(dom, dom_ms, peaks, peak_src, clk)
+    per_part = {name: {"ms": round(part_ms[name] / args.steps, 4)} for name in part_ms}
+    for name, units, _ in parts:
+        if units:
+            per_part[name]["osc_steps_per_s"] = units / (part_ms[name] / args.steps / 1e3)
+        else:
+            per_part[name]["numbers_per_s"] = FILL_N / (part_ms[name] / args.steps / 1e3)
+            per_part[name]["GBps"] = FILL_N * 4 / (part_ms[name] / args.steps / 1e3) / 1e9
+
+    line = {
+        "metric": "oscillator-steps/s (fused LD+RNG, all generators, whole hot path)",
+        "value": value,
+        "unit": "oscillator-steps/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+u32",
+        "data": "synthetic (seeded oscillators; equilibrium start)",
+        "config": {"workload": "N=1e6 3-D oscillators x 1e4 fused steps per generator "
+                               "(Taus, Ran2, Lagged Fibonacci row 9) + 2^30 uniform and "
+                               "2^30 normal fills per generator",
+                   "n_oscillators": N_OSC, "ld_steps": LD_STEPS, "fill_numbers": FILL_N,
+                   "params": PARAMS, "l2": "flushed (256 MiB write) before every part",
+                   "parallelism": f"replicas x{world} (independent seeds, no collective)"},
+        "clocks": clk,
+        "gpu_launches": gpu_launches(parts, args.steps),
+        "e2e": e2e,
+        "roofline": roof,
+        "parts": per_part,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(parts, part_ms, args.steps)
+    return line
+
+
+def gpu_launches(parts, steps):
+    """Kernels of ours launched per timed step: one persistent kernel per fused
+    run plus the statistics finisher, one kernel per fill."""
+    n = 0
+    for name, _, _ in parts:
+        n += 2 if name.startswith("ld_") else 1
+    return n * steps
+
+
+def run_e2e(args, wl, parts, G, torch):
+    """The same step with inputs in pinned host memory: x, v of every fused
+    system copied host->device before and device->host after its run (plus
+    its statistics); each fill's first 4 KiB read back to the host."""
+    host = {}
+    for kind, s in wl.systems.items():
+        host[kind] = (s.x.cpu().pin_memory(), s.v.cpu().pin_memory())
+    probe = torch.empty(1024, dtype=torch.float32).pin_memory()
+    h2d = d2h = 0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        h2d = d2h = 0
+        for name, _, fn in parts:
+            if name.startswith("ld_"):
+                kind = name[3:]
+                s = wl.systems[kind]
+                hx, hv = host[kind]
+                s.x.copy_(hx, non_blocking=True)
+                s.v.copy_(hv, non_blocking=True)
+                fn()
+                hx.copy_(s.x, non_blocking=True)
+                hv.copy_(s.v, non_blocking=True)
+                h2d += 2 * hx.numel() * 4
+                d2h += 2 * hx.numel() * 4 + 40
+            else:
+                fn()
+                probe.copy_(wl.out[:1024], non_blocking=True)
+                d2h += 4096
+        torch.cuda.synchronize()
+    sec = (time.perf_counter() - t0) / args.steps
+    osc = sum(p[1] for p in parts)
+    return {"value": osc / sec, "unit": "oscillator-steps/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h}
+
+
+def roofline(part, ms, peaks, src, clk):
+    mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    kind = part.split("_")[-1]
+    if part.startswith("fill_"):
+        achieved = FILL_N * FILL_BYTES_PER_NUMBER / (ms / 1e3) / 1e9
+        peak = peaks["hbm_gbs"]
+        return {"kernel": part, "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{src} hbm_gbs (copy bandwidth)"}
+    if kind == "lagfib":
+        achieved = N_OSC * LD_STEPS * LFG_BYTES_PER_OSC_STEP / (ms / 1e3) / 1e9
+        peak = peaks["hbm_gbs"]
+        return {"kernel": part, "bound": "hbm", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": f"{src} hbm_gbs; algorithmic 96 B per oscillator-step"}
+    ops = INT_OPS_PER_OSC_STEP[kind] * N_OSC * LD_STEPS
+    achieved = ops / (ms / 1e3) / 1e12
+    peak = SMS * INT32_LANES_PER_SM * mhz * 1e6 / 1e12
+    return {"kernel": part, "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
+            "peak_source": f"152 SMs x {INT32_LANES_PER_SM} INT32 lanes x {mhz} MHz "
+                           f"(median SM clock under load)"}
+
+
+# --------------------------------------------------------------------- CPU
+def _oracle_rates(budget_scale=1.0):
+    """Time the oracle as it stands (one host core) on bounded samples of the
+    workload; returns per-part rates."""
+    import numpy as np
+    import oracle
+    p = oracle.params(**PARAMS)
+    rates = {}
+    n_pt, steps_pt = int(20000 * budget_scale), 100
+    for kind in KINDS:
+        if kind == "lagfib":
+            g = oracle.Gen(kind, SEED, N_OSC)
+            x, v = oracle.ld_init_eq_f32(g, N_OSC, p)
+            steps = max(1, int(2 * budget_scale))
+            t0 = time.perf_counter()
+            oracle.ld_run_f32(g, x, v, p, steps)
+            rates[f"ld_{kind}"] = N_OSC * steps / (time.perf_counter() - t0)
+        else:
+            g = oracle.Gen(kind, SEED, n_pt)
+            x, v = oracle.ld_init_eq_f32(g, n_pt, p)
+            t0 = time.perf_counter()
+            oracle.ld_run_f32(g, x, v, p, steps_pt)
+            rates[f"ld_{kind}"] = n_pt * steps_pt / (time.perf_counter() - t0)
+        nf = int(2 * 10**6 * budget_scale)
+        g = oracle.Gen(kind, SEED + 7, N_OSC if kind == "lagfib" else 4096)
+        t0 = time.perf_counter()
+        g.fill_uniform(nf)
+        rates[f"fill_uniform_{kind}"] = nf / (time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        g.fill_normal(nf)
+        rates[f"fill_normal_{kind}"] = nf / (time.perf_counter() - t0)
+    np.asarray(0)
+    return rates
+
+
+def _cpu_step_seconds(rates):
+    sec = 0.0
+    for name, r in rates.items():
+        units = N_OSC * LD_STEPS if name.startswith("ld_") else FILL_N
+        sec += units / r
+    return sec
+
+
+def _sample_text(scale):
+    return (f"per generator: Taus/Ran2 {int(20000 * scale)} oscillators x 100 steps, Lagged "
+            f"Fibonacci all 1e6 oscillators x {max(1, int(2 * scale))} steps, "
+            f"{int(2e6 * scale)} uniform + {int(2e6 * scale)} normal fill numbers; "
+            f"extrapolated per unit to the full step")
+
+
+def cpu_baseline(parts, part_ms, steps):
+    rates = _oracle_rates(1.0)
+    sec = _cpu_step_seconds(rates)
+    return {"value": N_OSC * LD_STEPS * 3 / sec, "unit": "oscillator-steps/s", "cores": 1,
+            "kind": "oracle", "sample": _sample_text(1.0),
+            "parts": {k: v for k, v in rates.items()}}
+
+
+def run_reference(args, world):
+    """The oracle on the host cores, timed like our arm: W untimed and K timed
+    steps, each a bounded sample of the workload extrapolated per unit."""
+    scale = 0.5
+    for _ in range(args.warmup):
+        _oracle_rates(0.1)
+    secs = []
+    t0 = time.perf_counter()
+    all_rates = []
+    for _ in range(args.steps):
+        rates = _oracle_rates(scale)
+        all_rates.append(rates)
+        secs.append(_cpu_step_seconds(rates))
+    wall = time.perf_counter() - t0
+    ms_per_step = 1e3 * statistics.mean(secs)
+    value = N_OSC * LD_STEPS * 3 / (ms_per_step / 1e3)
+    return {
+        "impl": "reference",
+        "metric": "oscillator-steps/s (fused LD+RNG, all generators, whole hot path)",
+        "value": value, "unit": "oscillator-steps/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+u32",
+        "data": "synthetic (seeded oscillators; equilibrium start)",
+        "config": {"workload": "N=1e6 3-D oscillators x 1e4 fused steps per generator "
+                               "(Taus, Ran2, Lagged Fibonacci row 9) + 2^30 uniform and "
+                               "2^30 normal fills per generator", "timed_wall_s": wall},
+        "cpu_baseline": {"value": value, "unit": "oscillator-steps/s", "cores": 1,
+                         "kind": "oracle", "sample": _sample_text(scale)},
+        "e2e": {"value": value, "unit": "oscillator-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+CASES = ("ld_taus", "ld_ran2", "ld_lagfib", "fill_uniform_taus", "fill_normal_taus",
+         "fill_uniform_ran2", "fill_normal_ran2", "fill_uniform_lagfib", "fill_normal_lagfib")
+
+
+def run_case(name: str):
+    """One small launch of one part (for profiler captures): fused runs use
+    2e5 oscillators x 200 steps, fills 2^28 numbers (1 GiB, larger than L2)."""
+    import torch
+    from paper_1003_1123_gb300 import gbrng as G
+    kind = name.split("_")[-1]
+    if name.startswith("ld_"):
+        n = 200000
+        r = G.rng_init(kind, SEED, n)
+        x = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+        v = torch.zeros_like(x)
+        s = G.LdSystem(r, x, v, **PARAMS)
+        G.ld_init_equilibrium(s)
+        for _ in range(2):
+            G.ld_run(s, 200)
+    else:
+        r = G.rng_init(kind, SEED, N_OSC)
+        out = torch.empty(2**28, dtype=torch.float32, device="cuda")
+        f = G.rng_fill_uniform if "uniform" in name else G.rng_fill_normal
+        for _ in range(2):
+            f(r, 2**28, out=out)
+    torch.cuda.synchronize()
+    print(f"case {name} done")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gbrng", choices=["gbrng", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--case", choices=CASES, help="run one small launch of one part and exit")
+    args = ap.parse_args()
+    if args.case:
+        run_case(args.case)
+        return
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps(run_reference(args, world)))
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    line = run_gpu(args, rank, world, dist)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

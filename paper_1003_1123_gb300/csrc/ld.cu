@@ -22,41 +22,6 @@ struct LdArgs {
     double* partials;  // [gridDim.x][4]
 };
 
-// Three normals of one particle-step from four draws of the generator.
-struct TausDraw {
-    uint4 y;
-    __device__ __forceinline__ void normals3(float& gx, float& gy, float& gz)
-    {
-        const float u1 = open01_from_u32(taus_next(y));
-        const float u2 = open01_from_u32(taus_next(y));
-        const float u3 = open01_from_u32(taus_next(y));
-        const float u4 = open01_from_u32(taus_next(y));
-        box_muller(u1, u2, gx, gy);
-        gz = box_muller_cos(u3, u4);
-    }
-};
-
-struct Ran2Draw {
-    Ran2Regs r;
-    int32_t* tab;
-    int T, tid;
-    __device__ __forceinline__ int32_t next()
-    {
-        int32_t* t = tab;
-        const int TT = T, ti = tid;
-        return ran2_next(r, [t, TT, ti](int j) -> int32_t& { return t[j * TT + ti]; });
-    }
-    __device__ __forceinline__ void normals3(float& gx, float& gy, float& gz)
-    {
-        const float u1 = u01_from_ran2(next());
-        const float u2 = u01_from_ran2(next());
-        const float u3 = u01_from_ran2(next());
-        const float u4 = u01_from_ran2(next());
-        box_muller(u1, u2, gx, gy);
-        gz = box_muller_cos(u3, u4);
-    }
-};
-
 template <int KIND, bool INIT>
 __global__ void __launch_bounds__(128) ld_pt_kernel(LdArgs a)
 {

@@ -1,0 +1,121 @@
+"""Batched persistent launch (one CUDA graph over many uneven systems): its
+trajectories and generator states equal one ld_run per system bit for bit,
+for every launch shape, and sampled oscillators match the oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1003_1123_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1003_1123_gb300 import gbrng
+    gbrng.lib()
+    return gbrng
+
+
+def make_systems(G, kind, specs, with_kper=False):
+    out = []
+    for i, sp in enumerate(specs):
+        r = G.rng_init(kind, sp["seed"], sp["n"])
+        x = torch.zeros((sp["n"], 3), dtype=torch.float32, device="cuda")
+        v = torch.zeros_like(x)
+        kp = None
+        if with_kper:
+            kp = torch.from_numpy(W.spring_constants(sp["n"], i)).cuda()
+        s = G.LdSystem(r, x, v, K=sp["K"], m=sp["m"], gamma=sp["gamma"], kT=sp["kT"], dt=sp["dt"],
+                       K_per=kp)
+        G.ld_init_equilibrium(s)
+        out.append(s)
+    return out
+
+
+def assert_same(G, a, b):
+    for sa, sb in zip(a, b):
+        assert torch.equal(sa.x, sb.x) and torch.equal(sa.v, sb.v)
+        assert G.rng_get_state(sa.rng) == G.rng_get_state(sb.rng)
+
+
+@pytest.mark.parametrize("kind", ["taus", "ran2"])
+@pytest.mark.parametrize("tune", [None, (64, 1, 0), (128, 2, 37), (256, 1, 100), (32, 2, 0)])
+def test_batched_equals_per_system(G, kind, tune):
+    specs = W.batched_systems(23, seed=5, n_lo=1, n_hi=3000)
+    a = make_systems(G, kind, specs, with_kper=True)
+    b = make_systems(G, kind, specs, with_kper=True)
+    steps = 301
+    sa = G.ld_run_batched(a, steps, tune=tune)
+    sb = [G.ld_run(s, steps) for s in b]
+    assert_same(G, a, b)
+    for x, y in zip(sa, sb):
+        for k in ("sum_x2", "sum_v2", "sum_xv", "energy_time_avg"):
+            assert math.isclose(x[k], y[k], rel_tol=1e-12, abs_tol=1e-9), (k, x[k], y[k])
+        assert x["steps"] == steps
+
+
+def test_batched_repeat_uses_cached_graph(G):
+    """Two calls in a row (same shape) continue every system exactly."""
+    specs = W.batched_systems(9, seed=8, n_lo=10, n_hi=500)
+    a = make_systems(G, "taus", specs)
+    b = make_systems(G, "taus", specs)
+    for _ in range(2):
+        G.ld_run_batched(a, 50, tune=(128, 1, 0))
+    for s in b:
+        G.ld_run(s, 100)
+    assert_same(G, a, b)
+
+
+def test_batched_rejects_mixed_or_shared_generators(G):
+    specs = W.batched_systems(2, seed=1, n_lo=10, n_hi=20)
+    a = make_systems(G, "taus", specs[:1]) + make_systems(G, "ran2", specs[1:])
+    with pytest.raises(G.GbrngError):
+        G.ld_run_batched(a, 10)
+    lfg = make_systems(G, "lagfib", specs)
+    with pytest.raises(G.GbrngError):
+        G.ld_run_batched(lfg, 10)
+
+
+def test_batched_paper_shaped_workload(G):
+    """512 systems, N log-uniform in [1e2, 1e5], K log-uniform in [0.1, 10],
+    gamma in [0.1, 2], kT in [0.5, 2], dt = 0.005, 5000 steps, Hybrid Taus,
+    autotuned shape: equal to per-system runs, sampled oscillators equal to
+    the oracle, equipartition of every large system within 5 sigma."""
+    specs = W.batched_systems(512, seed=1234)
+    steps = 5000
+    a = make_systems(G, "taus", specs)
+    x0 = [s.x.cpu().numpy().copy() for s in a]
+    v0 = [s.v.cpu().numpy().copy() for s in a]
+    st = G.ld_run_batched(a, steps)
+    # per-system comparison on a subset (all 512 would only repeat it)
+    pick = list(range(0, 512, 37))
+    b = make_systems(G, "taus", [specs[i] for i in pick])
+    for s in b:
+        G.ld_run(s, steps)
+    assert_same(G, [a[i] for i in pick], b)
+    # oracle on sampled oscillators of a few systems
+    for i in pick[:5]:
+        sp = specs[i]
+        g = oracle.Gen("taus", sp["seed"], sp["n"])
+        p = oracle.params(K=sp["K"], m=sp["m"], gamma=sp["gamma"], kT=sp["kT"], dt=sp["dt"])
+        xo, vo = oracle.ld_init_eq_f32(g, sp["n"], p)
+        assert np.abs(xo - x0[i]).max() <= 1e-6 * np.sqrt((xo.astype(float) ** 2).mean())
+        rows = np.unique(np.array([0, sp["n"] // 2, sp["n"] - 1]))
+        sub = oracle.Gen("taus", sp["seed"], len(rows))
+        sub.state[:] = g.state[rows]
+        xs, vs = xo[rows].copy(), vo[rows].copy()
+        oracle.ld_run_f32(sub, xs, vs, p, steps)
+        ref = max(np.sqrt((xs.astype(float) ** 2).mean()), 1e-30)
+        assert np.abs(a[i].x.cpu().numpy()[rows] - xs).max() / ref < 1e-5
+    for sp, s in zip(specs, st):
+        if sp["n"] < 20000:
+            continue
+        S = oracle.em_covariance(sp["K"], sp["m"], sp["gamma"], sp["kT"], sp["dt"], steps)
+        cnt = 3 * sp["n"]
+        assert abs(s["sum_x2"] / cnt - S[0, 0]) < 5 * S[0, 0] * math.sqrt(2 / cnt)
