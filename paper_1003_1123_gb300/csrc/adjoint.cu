@@ -125,10 +125,8 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs a)
                 if (KIND == GBRNG_TAUS) td.normals3(g[0], g[1], g[2]); else rd.normals3(g[0], g[1], g[2]);
 #pragma unroll
                 for (int q = 0; q < 3; ++q) em_component(c.cdt, c.cva, ckx, c.cs, g[q], x[q], v[q]);
-                const float xx = x[0] * x[0] + x[1] * x[1] + x[2] * x[2];
-                const float vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
-                loss.add(hK * xx + c.hm * vv);
-                xsq.add(xx);
+                loss.add(energy3(hK, c.hm, x[0], x[1], x[2], v[0], v[1], v[2]));
+                xsq.add(__fmaf_rn(x[2], x[2], __fmaf_rn(x[1], x[1], __fmul_rn(x[0], x[0]))));
             }
         }
         // end state: the system advances exactly as ld_run would

@@ -89,9 +89,7 @@ __global__ void __launch_bounds__(256) batched_kernel(const SysDesc* __restrict_
                 em_component(c.cdt, c.cva, ckx[j], c.cs, g0, x0[j], v0[j]);
                 em_component(c.cdt, c.cva, ckx[j], c.cs, g1, x1[j], v1[j]);
                 em_component(c.cdt, c.cva, ckx[j], c.cs, g2, x2[j], v2[j]);
-                const float xx = x0[j] * x0[j] + x1[j] * x1[j] + x2[j] * x2[j];
-                const float vv = v0[j] * v0[j] + v1[j] * v1[j] + v2[j] * v2[j];
-                e[j].add(hK[j] * xx + c.hm * vv);
+                e[j].add(energy3(hK[j], c.hm, x0[j], x1[j], x2[j], v0[j], v1[j], v2[j]));
             }
         }
         double acc[4] = {0, 0, 0, 0};
@@ -353,14 +351,15 @@ static int autotune(const ld_system* sys, int n_sys, int kind, const std::vector
 {
     const int64_t probe_steps = std::min<int64_t>(std::max<int64_t>(n_steps, 1), 64);
     // scratch: x, v (n*3 floats each) and the generator states
+    // every sub-buffer starts on a 256-byte boundary (Taus states are uint4)
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
     size_t bytes = 0;
     std::vector<size_t> off(n_sys);
     for (int s = 0; s < n_sys; ++s) {
         off[s] = bytes;
         const int64_t S = sys[s].rng->n;
-        bytes += sizeof(float) * 6 * sys[s].n;
-        bytes += kind == GBRNG_TAUS ? sizeof(uint4) * S : sizeof(int32_t) * 35 * S;
-        bytes = (bytes + 255) & ~(size_t)255;
+        bytes += 2 * up(sizeof(float) * 3 * sys[s].n);
+        bytes += up(kind == GBRNG_TAUS ? sizeof(uint4) * S : sizeof(int32_t) * 35 * S);
     }
     char* scratch = nullptr;
     if (cudaMalloc(&scratch, bytes) != cudaSuccess) {
@@ -373,8 +372,8 @@ static int autotune(const ld_system* sys, int n_sys, int kind, const std::vector
         char* b = scratch + off[s];
         const int64_t n = sys[s].n, S = sys[s].rng->n;
         copy[s].x = (float*)b;
-        copy[s].v = (float*)(b + sizeof(float) * 3 * n);
-        char* stt = b + sizeof(float) * 6 * n;
+        copy[s].v = (float*)(b + up(sizeof(float) * 3 * n));
+        char* stt = b + 2 * up(sizeof(float) * 3 * n);
         cudaMemcpyAsync(copy[s].x, sys[s].x, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, st);
         cudaMemcpyAsync(copy[s].v, sys[s].v, sizeof(float) * 3 * n, cudaMemcpyDeviceToDevice, st);
         hcopy[s].n = S;

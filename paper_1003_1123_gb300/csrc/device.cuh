@@ -162,6 +162,16 @@ __device__ __forceinline__ void em_component(float cdt, float cva, float ckx, fl
     v = vn;
 }
 
+// Energy (m|v|^2 + K|x|^2)/2 of one oscillator with a fixed operation order
+// (hK = K/2, hm = m/2), so every kernel accumulates identical values.
+__device__ __forceinline__ float energy3(float hK, float hm, float x0, float x1, float x2, float v0,
+                                         float v1, float v2)
+{
+    const float xx = __fmaf_rn(x2, x2, __fmaf_rn(x1, x1, __fmul_rn(x0, x0)));
+    const float vv = __fmaf_rn(v2, v2, __fmaf_rn(v1, v1, __fmul_rn(v0, v0)));
+    return __fmaf_rn(hK, xx, __fmul_rn(hm, vv));
+}
+
 // Kahan-compensated binary32 accumulator.
 struct Kahan {
     float s = 0.f, c = 0.f;

@@ -69,9 +69,7 @@ __global__ void __launch_bounds__(128) ld_pt_kernel(LdArgs a)
                 em_component(c.cdt, c.cva, ckx, c.cs, g0, x0, v0);
                 em_component(c.cdt, c.cva, ckx, c.cs, g1, x1, v1);
                 em_component(c.cdt, c.cva, ckx, c.cs, g2, x2, v2);
-                const float xx = x0 * x0 + x1 * x1 + x2 * x2;
-                const float vv = v0 * v0 + v1 * v1 + v2 * v2;
-                e.add(hK * xx + c.hm * vv);
+                e.add(energy3(hK, c.hm, x0, x1, x2, v0, v1, v2));
             }
         }
         a.x[3 * i] = x0, a.x[3 * i + 1] = x1, a.x[3 * i + 2] = x2;

@@ -1,28 +1,41 @@
 // Additive Lagged Fibonacci generator shared by all threads (Algorithm 3):
-//   x_p = x_{p-ll} + x_{p-(ll-sl)}  mod 2^32.
+//   x_p = x_{p-ll} + x_{p-D}  mod 2^32,   D = ll - sl.
 //
-// The sequence is walked in chunks of consecutive positions by a persistent
-// cooperative grid: chunk k goes to CTA k mod G, and each CTA takes its chunks
-// in increasing order.  Position p lives in ring[p & mask] (a power-of-two ring
-// of R >= ll + 8192 words, so no modulo and aligned writes).  A chunk may start
-// once every chunk that
-//   - wrote the values it reads (positions p - ll and p - (ll - sl)), and
-//   - read the values it overwrites (positions p - R + ll and p - R + ll - sl)
-// has finished.  Chunks are never wider than ll - sl, so those are always
-// earlier chunks; because every CTA is resident and works in chunk order, the
-// lowest unfinished chunk can always proceed.  CTA g publishes how many of
-// its chunks are done in ring_done[g] (release) -- chunk j is done iff
-// ring_done[j mod G] > j div G.  For the fused Langevin step a second counter
-// osc_done[g] is released after the oscillators of a chunk are written, so
-// the same oscillators' next step (chunk k - M) can be awaited.  Every wait is
-// bounded by %globaltimer; a wait that runs out records a timeout in the
-// status word and the kernel returns.
+// Leap.  Applying the recurrence to both terms gives, for p >= ll,
+//   x_p = x_{p-2ll} + 2 x_{p-ll-D} + x_{p-2D}  mod 2^32,
+// the same value with the nearest dependency twice as far back (2D instead of
+// D), so twice as many positions can be in flight.  Positions below ll (the
+// first ll values after seeding) use the recurrence itself.
+//
+// Schedule.  The sequence is cut into chunks of consecutive positions (fills)
+// or of one step of C oscillators (fused Langevin step, 4 positions each).  A
+// persistent cooperative grid of G CTAs takes chunk k on CTA k mod G, each CTA
+// in increasing order.  Position p lives in ring[p & mask], a power-of-two ring
+// of R >= 2 ll + 16384 words.  A chunk may start when every chunk that wrote a
+// value it reads, and every chunk that reads a value it overwrites (position
+// p - R), has finished; CTA g publishes the count of its finished chunks in
+// ring_done[g] (release), so chunk j is finished iff ring_done[j mod G] > j/G.
+// For the fused step the oscillators of chunk k were last written by chunk
+// k - M (same oscillators, previous step); osc_done[] tracks that.
+//
+// Pipeline.  While chunk k is computed from shared memory, the lag windows
+// (two or three contiguous ring ranges), x, v and K of chunk k + G are already
+// streaming into the other shared-memory stage with cp.async.  G is kept
+// below the dependency distance in chunks, so the dependencies of chunk k + G
+// never include a chunk of the same CTA that is not yet finished; the lowest
+// unfinished chunk can therefore always proceed.  Every wait is bounded by
+// %globaltimer; a wait that runs out records GBRNG_ETIMEOUT and the kernel
+// returns.
+#include <algorithm>
+
 #include "device.cuh"
 #include "internal.cuh"
 
 namespace gb {
 
 enum { LFG_U32 = 0, LFG_UNIFORM = 1, LFG_NORMAL = 2, LFG_LD = 3, LFG_LD_INIT = 4 };
+
+constexpr int kLfgThreads = 256;
 
 struct LfgArgs {
     uint32_t* ring;
@@ -32,8 +45,11 @@ struct LfgArgs {
     int64_t n_units;       // fill: numbers; LD: oscillators N
     int64_t n_steps;       // LD: steps (init: 2)
     int64_t C;             // fill: positions per chunk; LD: oscillators per chunk
+    int64_t Cpos;          // positions per chunk (fill: C, LD: 4C)
     int64_t M;             // LD: chunks per step
     int64_t total_chunks;
+    int lookahead;         // 1: prefetch chunk k + G while chunk k computes
+    int win_words;         // shared words per lag window (Cpos + 8)
     void* out;
     float* x;
     float* v;
@@ -47,6 +63,17 @@ struct LfgArgs {
     int64_t stall_chunk;   // test hook: this chunk's CTA stops publishing (-1: none)
 };
 
+// ---------------------------------------------------------------- cp.async
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// ------------------------------------------------------------ chunk geometry
 template <int MODE>
 __device__ __forceinline__ void chunk_range(const LfgArgs& a, int64_t k, int64_t& P0, int64_t& P1,
                                             int64_t& t, int64_t& o0)
@@ -76,13 +103,13 @@ __device__ __forceinline__ int64_t chunk_of(const LfgArgs& a, int64_t q)
     return t * a.M + o / a.C;
 }
 
-// Spin (bounded) until chunk j is done according to counter array `done`.
+// Bounded spin until chunk j is finished according to counter array `done`.
 __device__ bool wait_chunk(const LfgArgs& a, const uint32_t* done, int64_t j, uint64_t deadline)
 {
     const int64_t G = gridDim.x;
     const uint32_t* p = done + (j % G);
     const uint32_t need = (uint32_t)(j / G) + 1u;
-    unsigned ns = 32;
+    unsigned ns = 16;
     while (ld_acquire_u32(p) < need) {
         if (ld_volatile_i32(a.status) != DEV_OK) return false;
         if (global_ns() > deadline) {
@@ -90,21 +117,134 @@ __device__ bool wait_chunk(const LfgArgs& a, const uint32_t* done, int64_t j, ui
             return false;
         }
         __nanosleep(ns);
-        if (ns < 512) ns <<= 1;
+        if (ns < 256) ns <<= 1;
     }
     return true;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(256) lfg_kernel(LfgArgs a)
+// Lag offsets of a chunk: the recurrence (2 windows) below position ll, the
+// leap (3 windows) from ll on.  Returns the number of windows.
+__device__ __forceinline__ int lag_offsets(const LfgArgs& a, int64_t P0, int64_t* off)
 {
-    extern __shared__ __align__(16) uint32_t vals[];   // values of the current chunk
+    const int64_t ll = a.ll, D = (int64_t)a.ll - a.sl;
+    if (P0 >= ll) {
+        off[0] = 2 * ll;
+        off[1] = ll + D;
+        off[2] = 2 * D;
+        return 3;
+    }
+    off[0] = ll;
+    off[1] = D;
+    off[2] = 0;
+    return 2;
+}
+
+// Warp 0 waits for every chunk chunk k depends on; returns false (on all
+// lanes) if a wait ran out.  Lanes 0-8: the ranges read (up to 3 windows x 3
+// chunks); lanes 9-23: readers of the overwritten positions p - R
+// (p - R + {D, ll, 2D, ll + D, 2 ll}); lane 24: the oscillators' previous step.
+template <int MODE>
+__device__ bool wait_deps(const LfgArgs& a, int64_t k)
+{
+    const int lane = threadIdx.x & 31;
+    int64_t P0, P1, t, o0;
+    chunk_range<MODE>(a, k, P0, P1, t, o0);
+    const int64_t R = (int64_t)a.mask + 1, ll = a.ll, D = (int64_t)a.ll - a.sl;
+    bool ok = true;
+    const uint64_t deadline = global_ns() + a.wait_ns;
+    int64_t off = -1;
+    int sub = 0;
+    if (lane < 9) {
+        int64_t offs[3];
+        const int nw = lag_offsets(a, P0, offs);
+        if (lane / 3 < nw) off = offs[lane / 3];
+        sub = lane % 3;
+    } else if (lane < 24) {
+        const int q = (lane - 9) / 3;
+        off = q == 0 ? R - D : q == 1 ? R - ll : q == 2 ? R - 2 * D : q == 3 ? R - ll - D : R - 2 * ll;
+        sub = (lane - 9) % 3;
+    }
+    if (off > 0) {
+        const int64_t q0 = max(P0 - off, a.base), q1 = P1 - off;
+        if (q1 > a.base) {
+            const int64_t j = chunk_of<MODE>(a, q0) + sub;
+            if (j <= chunk_of<MODE>(a, q1 - 1)) ok = wait_chunk(a, a.ring_done, j, deadline);
+        }
+    } else if (lane == 24 && MODE >= LFG_LD && k - a.M >= 0) {
+        ok = wait_chunk(a, a.osc_done, k - a.M, deadline);
+    }
+    return !__any_sync(0xffffffffu, !ok);
+}
+
+// Stage layout (32-bit words): 3 lag windows of win_words, then (LD) x[3C],
+// v[3C], K[C].
+__device__ __forceinline__ size_t stage_words(const LfgArgs& a, bool ld)
+{
+    return 3 * (size_t)a.win_words + (ld ? 7 * (size_t)a.C : 0);
+}
+
+// All threads: start the async copies of chunk k into `stage`.  Lag window w
+// starts at position P0 - off_w; it is fetched from the 16-byte-aligned word
+// below, so its values sit at stage[w*win + shift_w + i].
+template <int MODE>
+__device__ void issue_copies(const LfgArgs& a, int64_t k, uint32_t* stage)
+{
+    int64_t P0, P1, t, o0;
+    chunk_range<MODE>(a, k, P0, P1, t, o0);
+    const int64_t len = P1 - P0;
+    int64_t offs[3];
+    const int nw = lag_offsets(a, P0, offs);
+    for (int w = 0; w < nw; ++w) {
+        const int64_t q0 = P0 - offs[w];
+        const uint64_t start = (uint64_t)q0 & ~(uint64_t)3;
+        const int shift = (int)((uint64_t)q0 & 3u);
+        const int nvec = (int)((len + shift + 3) >> 2);
+        uint32_t* dst = stage + (size_t)w * a.win_words;
+        for (int j = threadIdx.x; j < nvec; j += blockDim.x)
+            cp_async16(dst + 4 * j, a.ring + ((start + 4 * (uint64_t)j) & a.mask));
+    }
+    if (MODE >= LFG_LD) {
+        const int64_t cnt = len >> 2;
+        float* sx = (float*)stage + 3 * (size_t)a.win_words;
+        float* sv = sx + 3 * a.C;
+        float* sk = sv + 3 * a.C;
+        if (MODE == LFG_LD) {
+            // x, v: 3*cnt floats from x + 3*o0 (o0 is a multiple of 4, so
+            // 16-byte aligned); the tail short of a vector is loaded directly.
+            const int64_t nf = 3 * cnt, nv4 = nf >> 2;
+            const float* gx = a.x + 3 * o0;
+            const float* gv = a.v + 3 * o0;
+            for (int64_t j = threadIdx.x; j < nv4; j += blockDim.x) {
+                cp_async16(sx + 4 * j, gx + 4 * j);
+                cp_async16(sv + 4 * j, gv + 4 * j);
+            }
+            for (int64_t j = 4 * nv4 + threadIdx.x; j < nf; j += blockDim.x) {
+                sx[j] = __ldcg(gx + j);
+                sv[j] = __ldcg(gv + j);
+            }
+        }
+        if (a.Kper) {
+            const int64_t nk4 = cnt >> 2;
+            for (int64_t j = threadIdx.x; j < nk4; j += blockDim.x)
+                cp_async16(sk + 4 * j, a.Kper + o0 + 4 * j);
+            for (int64_t j = 4 * nk4 + threadIdx.x; j < cnt; j += blockDim.x)
+                sk[j] = __ldcg(a.Kper + o0 + j);
+        }
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kLfgThreads) lfg_kernel(LfgArgs a)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
     __shared__ double red[4 * 32];
     __shared__ int s_abort;
+    constexpr bool LD = MODE >= LFG_LD;
     const int tid = threadIdx.x, T = blockDim.x;
     const int64_t G = gridDim.x;
-    const int64_t R = (int64_t)a.mask + 1;
-    const int64_t offs[4] = {a.ll, a.ll - a.sl, R - a.ll + a.sl, R - a.ll};
+    const size_t sw = stage_words(a, LD);
+    uint32_t* stages[2] = {smem, smem + sw};
+    uint32_t* vals = smem + 2 * sw;          // values of the chunk being consumed
     uint32_t done_count = 0;
     bool publish = true;
     Kahan e;
@@ -112,35 +252,45 @@ __global__ void __launch_bounds__(256) lfg_kernel(LfgArgs a)
     if (tid == 0) s_abort = 0;
     __syncthreads();
 
-    for (int64_t k = blockIdx.x; k < a.total_chunks; k += G) {
-        int64_t P0, P1, t, o0;
-        chunk_range<MODE>(a, k, P0, P1, t, o0);
-        // ---- wait for the chunks this one depends on (warp 0, one lane each)
-        if (tid < 32) {
-            bool ok = true;
-            const uint64_t deadline = global_ns() + a.wait_ns;
-            if (tid < 12) {
-                const int64_t off = offs[tid / 3];
-                const int64_t q0 = max(P0 - off, a.base), q1 = P1 - off;
-                if (q1 > a.base) {
-                    const int64_t j = chunk_of<MODE>(a, q0) + tid % 3;
-                    if (j <= chunk_of<MODE>(a, q1 - 1)) ok = wait_chunk(a, a.ring_done, j, deadline);
-                }
-            } else if (tid == 12 && MODE >= LFG_LD && k - a.M >= 0) {
-                ok = wait_chunk(a, a.osc_done, k - a.M, deadline);
-            }
-            if (__any_sync(0xffffffffu, !ok) && tid == 0) s_abort = 1;
-        }
+    // prologue: the first chunk
+    int64_t k = blockIdx.x;
+    if (k < a.total_chunks) {
+        if (tid < 32 && !wait_deps<MODE>(a, k) && tid == 0) s_abort = 1;
         __syncthreads();
         if (s_abort) return;
+        issue_copies<MODE>(a, k, stages[0]);
+    }
+    cp_async_commit();
+    int s = 0;
+    for (; k < a.total_chunks; k += G, s ^= 1) {
+        const int64_t kn = k + G;
+        const bool pre = a.lookahead && kn < a.total_chunks;
+        if (pre) {
+            if (tid < 32 && !wait_deps<MODE>(a, kn) && tid == 0) s_abort = 1;
+            __syncthreads();
+            if (s_abort) {
+                cp_async_wait<0>();
+                return;
+            }
+            issue_copies<MODE>(a, kn, stages[s ^ 1]);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
 
-        // ---- generate the chunk's values, element-wise and coalesced
+        // ---- values of chunk k from the staged lag windows
+        int64_t P0, P1, t, o0;
+        chunk_range<MODE>(a, k, P0, P1, t, o0);
         const int64_t len = P1 - P0;
-        for (int64_t i = tid; i < len; i += T) {
+        int64_t offs[3];
+        const int nw = lag_offsets(a, P0, offs);
+        const uint32_t* st = stages[s];
+        const uint32_t* w0 = st + ((uint64_t)(P0 - offs[0]) & 3u);
+        const uint32_t* w1 = st + a.win_words + ((uint64_t)(P0 - offs[1]) & 3u);
+        const uint32_t* w2 = st + 2 * a.win_words + ((uint64_t)(P0 - offs[2]) & 3u);
+        for (int i = tid; i < len; i += T) {
             const int64_t q = P0 + i;
-            const uint32_t xl = __ldcg(a.ring + ((uint64_t)(q - a.ll) & a.mask));
-            const uint32_t xs = __ldcg(a.ring + ((uint64_t)(q - (a.ll - a.sl)) & a.mask));
-            const uint32_t val = xl + xs;
+            const uint32_t val = nw == 3 ? w0[i] + 2u * w1[i] + w2[i] : w0[i] + w1[i];
             __stcg(a.ring + ((uint64_t)q & a.mask), val);
             if (MODE == LFG_U32)
                 __stcs((uint32_t*)a.out + (q - a.base), val);
@@ -151,12 +301,9 @@ __global__ void __launch_bounds__(256) lfg_kernel(LfgArgs a)
         }
         __syncthreads();
         if (k == a.stall_chunk) publish = false;
-        if (tid == 0 && publish) {
-            __threadfence();
-            st_release_u32(a.ring_done + blockIdx.x, done_count + 1u);
-        }
+        if (tid == 0 && publish) st_release_u32(a.ring_done + blockIdx.x, done_count + 1u);
 
-        // ---- consume the values (pairs / oscillators) from shared memory
+        // ---- consume the values (pairs / oscillators)
         if (MODE == LFG_NORMAL) {
             const int64_t pairs = len >> 1, e0 = (P0 - a.base) >> 1;
             for (int64_t p = tid; p < pairs; p += T) {
@@ -164,40 +311,41 @@ __global__ void __launch_bounds__(256) lfg_kernel(LfgArgs a)
                 box_muller(open01_from_u32(vals[2 * p]), open01_from_u32(vals[2 * p + 1]), g.x, g.y);
                 __stcs((float2*)a.out + (e0 + p), g);
             }
-        } else if (MODE >= LFG_LD) {
+        } else if (LD) {
             const int64_t cnt = len >> 2;
+            const float* sx = (const float*)st + 3 * (size_t)a.win_words;
+            const float* sv = sx + 3 * a.C;
+            const float* sk = sv + 3 * a.C;
             for (int64_t o = tid; o < cnt; o += T) {
                 const int64_t i = o0 + o;
                 const uint4 w = *reinterpret_cast<const uint4*>(vals + 4 * o);
                 float g0, g1, g2;
                 box_muller(open01_from_u32(w.x), open01_from_u32(w.y), g0, g1);
                 g2 = box_muller_cos(open01_from_u32(w.z), open01_from_u32(w.w));
-                const float Ki = a.Kper ? __ldcg(a.Kper + i) : a.c.K;
+                const float Ki = a.Kper ? sk[o] : a.c.K;
                 float* xp = a.x + 3 * i;
                 float* vp = a.v + 3 * i;
                 if (MODE == LFG_LD_INIT) {
                     if (t == 0) {
-                        const float sx = __fsqrt_rn(__fdiv_rn(a.c.kT, Ki));
-                        __stcg(xp, __fmul_rn(sx, g0));
-                        __stcg(xp + 1, __fmul_rn(sx, g1));
-                        __stcg(xp + 2, __fmul_rn(sx, g2));
+                        const float sxx = __fsqrt_rn(__fdiv_rn(a.c.kT, Ki));
+                        __stcg(xp, __fmul_rn(sxx, g0));
+                        __stcg(xp + 1, __fmul_rn(sxx, g1));
+                        __stcg(xp + 2, __fmul_rn(sxx, g2));
                     } else {
                         __stcg(vp, __fmul_rn(a.c.sv, g0));
                         __stcg(vp + 1, __fmul_rn(a.c.sv, g1));
                         __stcg(vp + 2, __fmul_rn(a.c.sv, g2));
                     }
                 } else {
-                    float x0 = __ldcg(xp), x1 = __ldcg(xp + 1), x2 = __ldcg(xp + 2);
-                    float v0 = __ldcg(vp), v1 = __ldcg(vp + 1), v2 = __ldcg(vp + 2);
+                    float x0 = sx[3 * o], x1 = sx[3 * o + 1], x2 = sx[3 * o + 2];
+                    float v0 = sv[3 * o], v1 = sv[3 * o + 1], v2 = sv[3 * o + 2];
                     const float ckx = __fmul_rn(a.c.ckm, Ki);
                     em_component(a.c.cdt, a.c.cva, ckx, a.c.cs, g0, x0, v0);
                     em_component(a.c.cdt, a.c.cva, ckx, a.c.cs, g1, x1, v1);
                     em_component(a.c.cdt, a.c.cva, ckx, a.c.cs, g2, x2, v2);
                     __stcg(xp, x0), __stcg(xp + 1, x1), __stcg(xp + 2, x2);
                     __stcg(vp, v0), __stcg(vp + 1, v1), __stcg(vp + 2, v2);
-                    const float xx = x0 * x0 + x1 * x1 + x2 * x2;
-                    const float vv = v0 * v0 + v1 * v1 + v2 * v2;
-                    e.add(0.5f * Ki * xx + a.c.hm * vv);
+                    e.add(energy3(0.5f * Ki, a.c.hm, x0, x1, x2, v0, v1, v2));
                     if (t == a.n_steps - 1) {
                         acc[0] += (double)x0 * x0 + (double)x1 * x1 + (double)x2 * x2;
                         acc[1] += (double)v0 * v0 + (double)v1 * v1 + (double)v2 * v2;
@@ -205,14 +353,23 @@ __global__ void __launch_bounds__(256) lfg_kernel(LfgArgs a)
                     }
                 }
             }
-            __syncthreads();
-            if (tid == 0 && publish) {
-                __threadfence();
-                st_release_u32(a.osc_done + blockIdx.x, done_count + 1u);
-            }
         }
+        __syncthreads();
+        if (LD && tid == 0 && publish) st_release_u32(a.osc_done + blockIdx.x, done_count + 1u);
         ++done_count;
+        if (!pre && k + G < a.total_chunks) {
+            // no lookahead: fetch the next chunk now
+            if (tid < 32 && !wait_deps<MODE>(a, k + G) && tid == 0) s_abort = 1;
+            __syncthreads();
+            if (s_abort) {
+                cp_async_wait<0>();
+                return;
+            }
+            issue_copies<MODE>(a, k + G, stages[s ^ 1]);
+            cp_async_commit();
+        }
     }
+    cp_async_wait<0>();
     if (MODE == LFG_LD && a.partials) {
         double v[4] = {acc[0], acc[1], acc[2], e.value()};
         block_reduce_sum<4>(v, red);
@@ -243,19 +400,35 @@ int lfg_seed(Handle* h, cudaStream_t st)
     return GBRNG_OK;
 }
 
+// Grid size: as many resident CTAs as fit, but fewer than the dependency
+// distance in chunks (and than the chunks per step for the fused step), so
+// that prefetching one round ahead never waits on the prefetching CTA itself.
 template <int MODE>
-static int launch(Handle* h, LfgArgs& a, int T, size_t smem, cudaStream_t st, int64_t* G_out)
+static int launch(Handle* h, LfgArgs& a, cudaStream_t st, int64_t* G_out)
 {
     DevInfo di;
     GB_CHECK(dev_info(h->device, &di));
+    constexpr bool LD = MODE >= LFG_LD;
     auto fn = lfg_kernel<MODE>;
-    if (smem > 48 * 1024) GB_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)smem));
+    a.win_words = (int)(a.Cpos + 8);
+    const size_t sw = 3 * (size_t)a.win_words + (LD ? 7 * (size_t)a.C : 0);
+    const size_t smem = sizeof(uint32_t) * (2 * sw + ((MODE == LFG_NORMAL || LD) ? a.Cpos : 0));
+    if (smem > di.smem_optin) return fail(GBRNG_EINVAL, "Lagged Fibonacci stage too large");
+    GB_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int occ = 0;
-    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, T, smem));
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kLfgThreads, smem));
     if (occ < 1) return fail(GBRNG_EINVAL, "Lagged Fibonacci kernel does not fit on an SM");
+    const int64_t D = (int64_t)h->ll - h->sl;
+    const int64_t R = (int64_t)h->ring_mask + 1;
+    const int64_t dist_pos = std::min<int64_t>(D, R - 2 * (int64_t)h->ll);   // nearest dependency
+    const int64_t delta = dist_pos / a.Cpos - 1;                              // in chunks (lower bound)
     int64_t G = (int64_t)di.sms * occ;
-    if (G > a.total_chunks) G = a.total_chunks;
+    G = std::min<int64_t>(G, a.total_chunks);
+    int64_t limit = delta;
+    if (LD) limit = std::min<int64_t>(limit, a.M);
+    a.lookahead = (limit - 1 >= 1) ? 1 : 0;
+    if (a.lookahead) G = std::min<int64_t>(G, limit - 1);
+    if (G < 1) G = 1;
     GB_CHECK(ensure_progress(h, 2 * G));
     if (MODE == LFG_LD) GB_CHECK(ensure_partials(h, G));
     a.ring_done = h->progress;
@@ -267,7 +440,8 @@ static int launch(Handle* h, LfgArgs& a, int T, size_t smem, cudaStream_t st, in
     GB_CUDA(cudaMemsetAsync(h->progress, 0, sizeof(uint32_t) * 2 * G, st));
     GB_CUDA(cudaMemsetAsync(h->dstatus, 0, sizeof(int), st));
     void* args[] = {&a};
-    GB_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3((unsigned)G), dim3(T), args, smem, st));
+    GB_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3((unsigned)G), dim3(kLfgThreads), args,
+                                        smem, st));
     *G_out = G;
     return GBRNG_OK;
 }
@@ -283,6 +457,13 @@ static int read_status(Handle* h, cudaStream_t st)
     return GBRNG_OK;
 }
 
+// Largest chunk allowed: no wider than the nearest dependency D = ll - sl.
+static int64_t max_chunk_positions(const Handle* h, int64_t want)
+{
+    const int64_t D = (int64_t)h->ll - h->sl;
+    return std::min<int64_t>(want, D);
+}
+
 int lfg_fill(Handle* h, void* dst, int64_t n, int mode, cudaStream_t st)
 {
     LfgArgs a{};
@@ -292,19 +473,18 @@ int lfg_fill(Handle* h, void* dst, int64_t n, int mode, cudaStream_t st)
     a.sl = h->sl;
     a.base = h->pos;
     a.n_units = n;
-    int64_t C = 4096;
-    if (C > h->ll - h->sl) C = (h->ll - h->sl) & ~(int64_t)1;
+    int64_t C = max_chunk_positions(h, 2048) & ~(int64_t)3;
     a.C = C;
+    a.Cpos = C;
     a.total_chunks = (n + C - 1) / C;
     a.out = dst;
-    const int T = 256;
     int64_t G = 0;
     if (mode == LFG_U32)
-        GB_CHECK(launch<LFG_U32>(h, a, T, 0, st, &G));
+        GB_CHECK(launch<LFG_U32>(h, a, st, &G));
     else if (mode == LFG_UNIFORM)
-        GB_CHECK(launch<LFG_UNIFORM>(h, a, T, 0, st, &G));
+        GB_CHECK(launch<LFG_UNIFORM>(h, a, st, &G));
     else
-        GB_CHECK(launch<LFG_NORMAL>(h, a, T, sizeof(uint32_t) * C, st, &G));
+        GB_CHECK(launch<LFG_NORMAL>(h, a, st, &G));
     GB_CHECK(read_status(h, st));
     h->pos += n;
     return GBRNG_OK;
@@ -343,6 +523,8 @@ int lfg_ld(const ld_system* s, int64_t n_steps, int init, ld_stats* out, cudaStr
         }
         return GBRNG_OK;
     }
+    if (((uintptr_t)s->x & 15u) || ((uintptr_t)s->v & 15u) || ((uintptr_t)s->K_per & 15u))
+        return fail(GBRNG_EINVAL, "Lagged Fibonacci systems need 16-byte aligned x, v, K_per");
     LfgArgs a{};
     a.ring = h->ring;
     a.mask = h->ring_mask;
@@ -351,23 +533,23 @@ int lfg_ld(const ld_system* s, int64_t n_steps, int init, ld_stats* out, cudaStr
     a.base = h->pos;
     a.n_units = s->n;
     a.n_steps = init ? 2 : n_steps;
-    int64_t C = 256;                                  // oscillators per chunk
-    if (4 * C > h->ll - h->sl) C = (h->ll - h->sl) / 4;
-    if (C > s->n) C = s->n;
+    int64_t C = max_chunk_positions(h, 4 * 512) / 4;   // oscillators per chunk
+    C &= ~(int64_t)3;
+    if (C < 4) C = 4;
+    if (C > s->n) C = (s->n + 3) & ~(int64_t)3;
     a.C = C;
+    a.Cpos = 4 * C;
     a.M = (s->n + C - 1) / C;
     a.total_chunks = a.M * a.n_steps;
     a.x = s->x;
     a.v = s->v;
     a.Kper = s->K_per;
     a.c = make_coef(s);
-    const int T = 256;
-    const size_t smem = sizeof(uint32_t) * 4 * C;
     int64_t G = 0;
     if (init)
-        GB_CHECK(launch<LFG_LD_INIT>(h, a, T, smem, st, &G));
+        GB_CHECK(launch<LFG_LD_INIT>(h, a, st, &G));
     else
-        GB_CHECK(launch<LFG_LD>(h, a, T, smem, st, &G));
+        GB_CHECK(launch<LFG_LD>(h, a, st, &G));
     GB_CHECK(read_status(h, st));
     h->pos += 4 * s->n * a.n_steps;
     if (out) return finish_stats(h, G, n_steps, out, st);

@@ -171,9 +171,10 @@ static int alloc_state(Handle* h)
     } else if (h->kind == GBRNG_RAN2) {
         e = cudaMalloc(&h->r2, sizeof(int32_t) * 35 * h->n);
     } else {
-        // ring size: power of two >= ll + 2 * largest chunk (4 * 1024 words)
+        // ring size: power of two >= 2 ll + 16384 words (the leap reads back
+        // to p - 2 ll; the margin keeps overwritten values far behind readers)
         uint64_t R = 1;
-        while (R < (uint64_t)h->ll + 8192u) R <<= 1;
+        while (R < 2 * (uint64_t)h->ll + 16384u) R <<= 1;
         h->ring_mask = (uint32_t)(R - 1);
         e = cudaMalloc(&h->ring, sizeof(uint32_t) * R);
     }
@@ -467,11 +468,20 @@ int rng_set_state(gbrng_t rng, const void* host, size_t bytes)
             for (int k = 0; k < 35; ++k) tmp[(size_t)k * rng->n + s] = in[35 * s + k];
         GB_CUDA(cudaMemcpy(rng->r2, tmp.data(), pb, cudaMemcpyHostToDevice));
     } else {
+        // The blob holds x_{p-ll} .. x_{p-1}.  The leap form of the recurrence
+        // also reads x_{p-2ll} .. x_{p-ll-1}; they follow from the recurrence
+        // run backwards, x_q = x_{q+ll} - x_{q+sl}, exact for every q >= -ll.
         const uint64_t R = (uint64_t)rng->ring_mask + 1;
-        std::vector<uint32_t> ring(R, 0u);
+        const int64_t ll = rng->ll, sl = rng->sl, p = hd.position;
+        std::vector<uint32_t> hist(2 * (size_t)ll);          // hist[j] = x_{p-2ll+j}
         const uint32_t* in = (const uint32_t*)src;
-        for (int64_t k = 0; k < rng->ll; ++k)
-            ring[(uint64_t)(hd.position - rng->ll + k) & rng->ring_mask] = in[k];
+        for (int64_t k = 0; k < ll; ++k) hist[ll + k] = in[k];
+        for (int64_t j = ll - 1; j >= 0; --j) hist[j] = hist[j + ll] - hist[j + sl];
+        std::vector<uint32_t> ring(R, 0u);
+        for (int64_t j = 0; j < 2 * ll; ++j) {
+            const int64_t q = p - 2 * ll + j;
+            if (q >= -ll) ring[(uint64_t)q & rng->ring_mask] = hist[j];
+        }
         GB_CUDA(cudaMemcpy(rng->ring, ring.data(), sizeof(uint32_t) * R, cudaMemcpyHostToDevice));
         rng->pos = hd.position;
     }

@@ -54,9 +54,11 @@ def test_batched_equals_per_system(G, kind, tune):
     sa = G.ld_run_batched(a, steps, tune=tune)
     sb = [G.ld_run(s, steps) for s in b]
     assert_same(G, a, b)
+    # statistics: same per-oscillator values summed in another order (and, when
+    # the steps are split over launches, Kahan sums restarted per launch)
     for x, y in zip(sa, sb):
         for k in ("sum_x2", "sum_v2", "sum_xv", "energy_time_avg"):
-            assert math.isclose(x[k], y[k], rel_tol=1e-12, abs_tol=1e-9), (k, x[k], y[k])
+            assert math.isclose(x[k], y[k], rel_tol=1e-9, abs_tol=1e-9), (k, x[k], y[k])
         assert x["steps"] == steps
 
 
