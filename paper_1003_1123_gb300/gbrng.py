@@ -74,6 +74,8 @@ SIGNATURES = {
     "ld_backward": (C.c_int, [C.POINTER(LdSystemC), C.c_int64, C.c_int, C.c_void_p,
                               C.POINTER(C.c_double), C.POINTER(C.c_double),
                               C.POINTER(C.c_double), C.c_void_p]),
+    "ld_run_noalloc": (C.c_int, [C.POINTER(LdSystemC), C.c_int64, C.POINTER(LdStatsC),
+                                 C.c_void_p]),
     "gbrng_last_error": (C.c_char_p, []),
 }
 
@@ -280,6 +282,16 @@ def ld_run(system: LdSystem, n_steps: int, stats: bool = True, stream=None):
     cs = system.c_struct()
     st = LdStatsC()
     _check(lib().ld_run(C.byref(cs), n_steps, C.byref(st) if stats else None, _stream(stream)))
+    return _stats(st) if stats else None
+
+
+def ld_run_noalloc(system: LdSystem, n_steps: int, stats: bool = True, stream=None):
+    """ld_run without any device allocation (per-thread generators); see the C
+    header for who needs it and what it shares."""
+    cs = system.c_struct()
+    st = LdStatsC()
+    _check(lib().ld_run_noalloc(C.byref(cs), n_steps, C.byref(st) if stats else None,
+                                _stream(stream)))
     return _stats(st) if stats else None
 
 
