@@ -68,6 +68,7 @@ def lib():
                 "or_taus_seed": (None, [u64, i64, vp]),
                 "or_ran2_seed": (None, [u64, i64, vp]),
                 "or_lfg_seed": (None, [u64, i32, vp]),
+                "or_seed_streams": (None, [C.c_int, u64, vp, i64, vp]),
                 "or_lfg_table": (C.c_int, [C.c_int, C.POINTER(i32), C.POINTER(i32)]),
                 "or_lfg_default_row": (C.c_int, [i64]),
                 "or_taus_next": (u32, [vp]),
@@ -158,6 +159,22 @@ class Gen:
             g.state = np.ascontiguousarray(ring, dtype=np.uint32).copy()
         s = _Gen()
         s.kind, s.sl, s.ll, s.n_streams, s.pos = LAGFIB, sl, ll, 1, 0
+        s.state = g.state.ctypes.data
+        g._g = s
+        return g
+
+    @classmethod
+    def streams(cls, kind, seed: int, indices) -> "Gen":
+        """Per-thread generator holding only the streams with the given indices
+        of a larger generator (stream s is seeded from counters 8s + k)."""
+        k = KIND_NAMES[kind] if isinstance(kind, str) else int(kind)
+        idx = np.ascontiguousarray(indices, dtype=np.int64)
+        g = cls.__new__(cls)
+        g.kind, g.seed, g.n = k, int(seed), len(idx)
+        g.state = np.zeros((len(idx), 4 if k == TAUS else 35), np.uint32 if k == TAUS else np.int32)
+        lib().or_seed_streams(k, g.seed, _ptr(idx), len(idx), _ptr(g.state))
+        s = _Gen()
+        s.kind, s.n_streams, s.pos = k, len(idx), 0
         s.state = g.state.ctypes.data
         g._g = s
         return g

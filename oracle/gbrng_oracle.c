@@ -127,6 +127,27 @@ void or_ran2_seed(uint64_t seed, int64_t n, int32_t* st)
     }
 }
 
+/* Seed the streams with the given indices (rows of st in that order), as
+ * or_taus_seed / or_ran2_seed would for those indices. */
+void or_seed_streams(int kind, uint64_t seed, const int64_t* idx, int64_t n, void* st)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        const uint64_t s = (uint64_t)idx[j];
+        if (kind == OR_TAUS) {
+            static const uint32_t lowest[3] = {2u, 8u, 16u};
+            uint32_t* y = (uint32_t*)st + 4 * j;
+            for (int k = 0; k < 4; ++k) {
+                uint32_t w = (uint32_t)or_splitmix64(seed, 8u * s + (uint64_t)k);
+                if (k < 3 && w < lowest[k]) w += lowest[k];
+                y[k] = w;
+            }
+        } else {
+            uint64_t w = or_splitmix64(seed, 8u * s);
+            ran2_init_one(1 + (int32_t)(w % (uint64_t)R2_IMM1), (int32_t*)st + 35 * j);
+        }
+    }
+}
+
 void or_lfg_seed(uint64_t seed, int32_t ll, uint32_t* ring)
 {
     for (int32_t w = 0; w < ll; ++w) ring[w] = (uint32_t)or_splitmix64(seed, (uint64_t)w);

@@ -41,6 +41,7 @@ uint64_t or_splitmix64(uint64_t seed, uint64_t idx);
 void     or_taus_seed(uint64_t seed, int64_t n, uint32_t* st);
 void     or_ran2_seed(uint64_t seed, int64_t n, int32_t* st);
 void     or_lfg_seed(uint64_t seed, int32_t ll, uint32_t* ring);
+void     or_seed_streams(int kind, uint64_t seed, const int64_t* idx, int64_t n, void* st);
 int      or_lfg_table(int row, int32_t* sl, int32_t* ll);   /* Table I */
 int      or_lfg_default_row(int64_t n_threads);
 

@@ -83,12 +83,14 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs a)
                     rd.r.idum = a.r2[i];
                     rd.r.idum2 = a.r2[a.streams + i];
                     rd.r.iy = a.r2[2 * a.streams + i];
+                    #pragma unroll 4
                     for (int j = 0; j < 32; ++j)
                         tab[j * blockDim.x + threadIdx.x] = a.r2[(3 + j) * a.streams + i];
                 } else {
                     rd.r.idum = __float_as_int(src[0]);
                     rd.r.idum2 = __float_as_int(src[stride]);
                     rd.r.iy = __float_as_int(src[2 * stride]);
+                    #pragma unroll 4
                     for (int j = 0; j < 32; ++j)
                         tab[j * blockDim.x + threadIdx.x] = __float_as_int(src[(3 + j) * stride]);
                 }
@@ -104,6 +106,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs a)
                 dst[0] = __int_as_float(rd.r.idum);
                 dst[stride] = __int_as_float(rd.r.idum2);
                 dst[2 * stride] = __int_as_float(rd.r.iy);
+                #pragma unroll 4
                 for (int j = 0; j < 32; ++j)
                     dst[(3 + j) * stride] = __int_as_float(tab[j * blockDim.x + threadIdx.x]);
             }
@@ -138,6 +141,7 @@ __global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs a)
             a.r2[i] = rd.r.idum;
             a.r2[a.streams + i] = rd.r.idum2;
             a.r2[2 * a.streams + i] = rd.r.iy;
+            #pragma unroll 4
             for (int j = 0; j < 32; ++j)
                 a.r2[(3 + j) * a.streams + i] = tab[j * blockDim.x + threadIdx.x];
         }

@@ -6,6 +6,8 @@
 
 #include <cstdint>
 
+#include "bm_coeffs.cuh"
+
 namespace gb {
 
 // ------------------------------------------------------------------ seeding
@@ -99,12 +101,73 @@ __device__ __forceinline__ float open01_from_u32(uint32_t raw)
     return __fmul_rn(__uint2float_rn((raw >> 8) | 1u), 0x1p-24f);
 }
 
+// ---------------------------------------------------------------- Box-Muller
+// The transcendentals of the transform, reduced to the ranges the generators
+// produce (u a positive normal binary32 below 1) with polynomial coefficients
+// fitted by fit_bm_coeffs.py; all within 2 ulp on those ranges.
+
+// -2 ln(u): u = 2^e m with m in [2/3, 4/3) (exponent split at the bits of 2/3),
+// f = m - 1 exact, ln m = f + f^2 R(f), ln u = e ln2 + ln m (ln2 in two parts).
+__device__ __forceinline__ float neg2log(float u)
+{
+    const int bits = __float_as_int(u);
+    const int e = (bits - 0x3f2aaaab) >> 23;
+    const float f = __fsub_rn(__int_as_float(bits - (e << 23)), 1.0f);
+    const float f2 = __fmul_rn(f, f);
+    const float f4 = __fmul_rn(f2, f2);
+    // Estrin's scheme for R(f) of degree 8
+    const float p01 = __fmaf_rn(kLogR[1], f, kLogR[0]);
+    const float p23 = __fmaf_rn(kLogR[3], f, kLogR[2]);
+    const float p45 = __fmaf_rn(kLogR[5], f, kLogR[4]);
+    const float p67 = __fmaf_rn(kLogR[7], f, kLogR[6]);
+    const float p03 = __fmaf_rn(p23, f2, p01);
+    const float p47 = __fmaf_rn(p67, f2, p45);
+    const float p48 = __fmaf_rn(kLogR[8], f4, p47);
+    const float R = __fmaf_rn(p48, f4, p03);
+    const float lnm = __fmaf_rn(f2, R, f);
+    const float ef = (float)e;
+    const float l = __fmaf_rn(ef, -0x1.05c610p-29f, __fmaf_rn(ef, 0x1.62e430p-1f, lnm));
+    return __fmul_rn(-2.0f, l);
+}
+
+// sqrt(y) for a positive normal y: reciprocal square root and one Newton step.
+__device__ __forceinline__ float sqrt_pos(float y)
+{
+    const float r = rsqrtf(y);
+    const float s = __fmul_rn(y, r);
+    const float d = __fmaf_rn(-s, s, y);
+    return __fmaf_rn(d, __fmul_rn(0.5f, r), s);
+}
+
+// sin and cos of 2 pi u for u in [0, 1): x = 4u and r = x - rint(x) are exact,
+// theta = (pi/2) r in [-pi/4, pi/4], sin = r S(r^2), cos = C(r^2), then the
+// quadrant q = rint(x) rotates the pair by q quarter turns.
+__device__ __forceinline__ void sincos2pi(float u, float& s, float& c)
+{
+    const float x = __fmul_rn(4.0f, u);
+    const float qf = rintf(x);
+    const float r = __fsub_rn(x, qf);
+    const int q = (int)qf;
+    const float z = __fmul_rn(r, r);
+    const float S = __fmaf_rn(__fmaf_rn(__fmaf_rn(kSinS[3], z, kSinS[2]), z, kSinS[1]), z, kSinS[0]);
+    const float st = __fmul_rn(r, S);
+    const float z2 = __fmul_rn(z, z);
+    const float c01 = __fmaf_rn(kCosC[1], z, kCosC[0]);
+    const float c23 = __fmaf_rn(kCosC[3], z, kCosC[2]);
+    const float ct = __fmaf_rn(__fmaf_rn(kCosC[4], z2, c23), z2, c01);
+    const bool swap = q & 1;
+    const float so = swap ? ct : st;
+    const float co = swap ? st : ct;
+    s = (q & 2) ? -so : so;
+    c = ((q + 1) & 2) ? -co : co;
+}
+
 // Box-Muller pair from two uniforms in (0, 1).
 __device__ __forceinline__ void box_muller(float u1, float u2, float& g1, float& g2)
 {
-    const float rho = sqrtf(-2.0f * logf(u1));
+    const float rho = sqrt_pos(neg2log(u1));
     float s, c;
-    sincospif(2.0f * u2, &s, &c);
+    sincos2pi(u2, s, c);
     g1 = __fmul_rn(rho, c);
     g2 = __fmul_rn(rho, s);
 }
@@ -112,8 +175,10 @@ __device__ __forceinline__ void box_muller(float u1, float u2, float& g1, float&
 // Only the cosine branch (third normal of a particle-step).
 __device__ __forceinline__ float box_muller_cos(float u1, float u2)
 {
-    const float rho = sqrtf(-2.0f * logf(u1));
-    return __fmul_rn(rho, cospif(2.0f * u2));
+    const float rho = sqrt_pos(neg2log(u1));
+    float s, c;
+    sincos2pi(u2, s, c);
+    return __fmul_rn(rho, c);
 }
 
 // Three normals of one particle-step from four draws of the generator.

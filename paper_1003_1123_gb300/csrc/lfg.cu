@@ -35,7 +35,8 @@ namespace gb {
 
 enum { LFG_U32 = 0, LFG_UNIFORM = 1, LFG_NORMAL = 2, LFG_LD = 3, LFG_LD_INIT = 4 };
 
-constexpr int kLfgThreads = 256;
+constexpr int kLfgThreads = 512;   // two CTAs per SM: 32 warps hide the phase latencies
+constexpr int kLfgMaxGrid = 1024;   // CTAs at most (size of the progress caches)
 
 struct LfgArgs {
     uint32_t* ring;
@@ -44,8 +45,11 @@ struct LfgArgs {
     int64_t base;          // first position of this launch
     int64_t n_units;       // fill: numbers; LD: oscillators N
     int64_t n_steps;       // LD: steps (init: 2)
-    int64_t C;             // fill: positions per chunk; LD: oscillators per chunk
+    int64_t C;             // fill: positions per chunk; LD: oscillators per chunk (2^logC)
+    int logC;
     int64_t Cpos;          // positions per chunk (fill: C, LD: 4C)
+    int64_t per_step;      // LD: positions per step (4N)
+    double inv_per_step;   // LD: 1 / per_step
     int64_t M;             // LD: chunks per step
     int64_t total_chunks;
     int lookahead;         // 1: prefetch chunk k + G while chunk k computes
@@ -79,38 +83,47 @@ __device__ __forceinline__ void chunk_range(const LfgArgs& a, int64_t k, int64_t
                                             int64_t& t, int64_t& o0)
 {
     if (MODE <= LFG_NORMAL) {
-        P0 = a.base + k * a.C;
+        P0 = a.base + (k << a.logC);
         P1 = min(P0 + a.C, a.base + a.n_units);
         t = 0;
         o0 = 0;
     } else {
-        t = k / a.M;
-        o0 = (k - t * a.M) * a.C;
+        t = (uint32_t)k / (uint32_t)a.M;   // chunk ids stay below 2^31
+        o0 = (k - t * a.M) << a.logC;
         const int64_t cnt = min(a.C, a.n_units - o0);
         P0 = a.base + 4 * (a.n_units * t + o0);
         P1 = P0 + 4 * cnt;
     }
 }
 
+// Chunk holding position q >= base.  The step index uses a double-precision
+// reciprocal corrected to the exact quotient (positions stay below 2^53).
 template <int MODE>
 __device__ __forceinline__ int64_t chunk_of(const LfgArgs& a, int64_t q)
 {
     const int64_t r = q - a.base;
-    if (MODE <= LFG_NORMAL) return r / a.C;
-    const int64_t per_step = 4 * a.n_units;
-    const int64_t t = r / per_step;
-    const int64_t o = (r - t * per_step) >> 2;
-    return t * a.M + o / a.C;
+    if (MODE <= LFG_NORMAL) return r >> a.logC;
+    int64_t t = (int64_t)((double)r * a.inv_per_step);
+    if (t * a.per_step > r) --t;
+    if ((t + 1) * a.per_step <= r) ++t;
+    const int64_t o = (r - t * a.per_step) >> 2;
+    return t * a.M + (o >> a.logC);
 }
 
 // Bounded spin until chunk j is finished according to counter array `done`.
-__device__ bool wait_chunk(const LfgArgs& a, const uint32_t* done, int64_t j, uint64_t deadline)
+// `known` caches, per CTA, the largest count this CTA has already acquired:
+// a dependency at or below it needs no new load (the earlier acquire and the
+// barriers since then already order this CTA's reads after its writes).
+__device__ bool wait_chunk(const LfgArgs& a, const uint32_t* done, uint32_t* known, int64_t j,
+                           uint64_t deadline)
 {
-    const int64_t G = gridDim.x;
-    const uint32_t* p = done + (j % G);
-    const uint32_t need = (uint32_t)(j / G) + 1u;
+    const uint32_t G = gridDim.x;
+    const uint32_t g = (uint32_t)j % G;
+    const uint32_t need = (uint32_t)j / G + 1u;
+    if (known[g] >= need) return true;
     unsigned ns = 16;
-    while (ld_acquire_u32(p) < need) {
+    uint32_t seen;
+    while ((seen = ld_acquire_u32(done + g)) < need) {
         if (ld_volatile_i32(a.status) != DEV_OK) return false;
         if (global_ns() > deadline) {
             atomicCAS(a.status, DEV_OK, DEV_TIMEOUT);
@@ -119,6 +132,7 @@ __device__ bool wait_chunk(const LfgArgs& a, const uint32_t* done, int64_t j, ui
         __nanosleep(ns);
         if (ns < 256) ns <<= 1;
     }
+    known[g] = seen;
     return true;
 }
 
@@ -144,7 +158,7 @@ __device__ __forceinline__ int lag_offsets(const LfgArgs& a, int64_t P0, int64_t
 // chunks); lanes 9-23: readers of the overwritten positions p - R
 // (p - R + {D, ll, 2D, ll + D, 2 ll}); lane 24: the oscillators' previous step.
 template <int MODE>
-__device__ bool wait_deps(const LfgArgs& a, int64_t k)
+__device__ bool wait_deps(const LfgArgs& a, int64_t k, uint32_t* known_ring, uint32_t* known_osc)
 {
     const int lane = threadIdx.x & 31;
     int64_t P0, P1, t, o0;
@@ -168,10 +182,11 @@ __device__ bool wait_deps(const LfgArgs& a, int64_t k)
         const int64_t q0 = max(P0 - off, a.base), q1 = P1 - off;
         if (q1 > a.base) {
             const int64_t j = chunk_of<MODE>(a, q0) + sub;
-            if (j <= chunk_of<MODE>(a, q1 - 1)) ok = wait_chunk(a, a.ring_done, j, deadline);
+            if (j <= chunk_of<MODE>(a, q1 - 1))
+                ok = wait_chunk(a, a.ring_done, known_ring, j, deadline);
         }
     } else if (lane == 24 && MODE >= LFG_LD && k - a.M >= 0) {
-        ok = wait_chunk(a, a.osc_done, k - a.M, deadline);
+        ok = wait_chunk(a, a.osc_done, known_osc, k - a.M, deadline);
     }
     return !__any_sync(0xffffffffu, !ok);
 }
@@ -234,11 +249,12 @@ __device__ void issue_copies(const LfgArgs& a, int64_t k, uint32_t* stage)
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kLfgThreads) lfg_kernel(LfgArgs a)
+__global__ void __launch_bounds__(kLfgThreads, 2) lfg_kernel(LfgArgs a)
 {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ double red[4 * 32];
     __shared__ int s_abort;
+    __shared__ uint32_t known_ring[kLfgMaxGrid], known_osc[kLfgMaxGrid];
     constexpr bool LD = MODE >= LFG_LD;
     const int tid = threadIdx.x, T = blockDim.x;
     const int64_t G = gridDim.x;
@@ -250,12 +266,13 @@ __global__ void __launch_bounds__(kLfgThreads) lfg_kernel(LfgArgs a)
     Kahan e;
     double acc[3] = {0, 0, 0};
     if (tid == 0) s_abort = 0;
+    for (int i = tid; i < kLfgMaxGrid; i += T) known_ring[i] = known_osc[i] = 0u;
     __syncthreads();
 
     // prologue: the first chunk
     int64_t k = blockIdx.x;
     if (k < a.total_chunks) {
-        if (tid < 32 && !wait_deps<MODE>(a, k) && tid == 0) s_abort = 1;
+        if (tid < 32 && !wait_deps<MODE>(a, k, known_ring, known_osc) && tid == 0) s_abort = 1;
         __syncthreads();
         if (s_abort) return;
         issue_copies<MODE>(a, k, stages[0]);
@@ -266,7 +283,7 @@ __global__ void __launch_bounds__(kLfgThreads) lfg_kernel(LfgArgs a)
         const int64_t kn = k + G;
         const bool pre = a.lookahead && kn < a.total_chunks;
         if (pre) {
-            if (tid < 32 && !wait_deps<MODE>(a, kn) && tid == 0) s_abort = 1;
+            if (tid < 32 && !wait_deps<MODE>(a, kn, known_ring, known_osc) && tid == 0) s_abort = 1;
             __syncthreads();
             if (s_abort) {
                 cp_async_wait<0>();
@@ -359,7 +376,7 @@ __global__ void __launch_bounds__(kLfgThreads) lfg_kernel(LfgArgs a)
         ++done_count;
         if (!pre && k + G < a.total_chunks) {
             // no lookahead: fetch the next chunk now
-            if (tid < 32 && !wait_deps<MODE>(a, k + G) && tid == 0) s_abort = 1;
+            if (tid < 32 && !wait_deps<MODE>(a, k + G, known_ring, known_osc) && tid == 0) s_abort = 1;
             __syncthreads();
             if (s_abort) {
                 cp_async_wait<0>();
@@ -423,6 +440,7 @@ static int launch(Handle* h, LfgArgs& a, cudaStream_t st, int64_t* G_out)
     const int64_t dist_pos = std::min<int64_t>(D, R - 2 * (int64_t)h->ll);   // nearest dependency
     const int64_t delta = dist_pos / a.Cpos - 1;                              // in chunks (lower bound)
     int64_t G = (int64_t)di.sms * occ;
+    G = std::min<int64_t>(G, kLfgMaxGrid);
     G = std::min<int64_t>(G, a.total_chunks);
     int64_t limit = delta;
     if (LD) limit = std::min<int64_t>(limit, a.M);
@@ -457,11 +475,15 @@ static int read_status(Handle* h, cudaStream_t st)
     return GBRNG_OK;
 }
 
-// Largest chunk allowed: no wider than the nearest dependency D = ll - sl.
-static int64_t max_chunk_positions(const Handle* h, int64_t want)
+// Largest power-of-two chunk (in units of `unit` positions) no wider than the
+// nearest dependency D = ll - sl and not above `want` units.
+static int log2_chunk(const Handle* h, int64_t want, int64_t unit)
 {
     const int64_t D = (int64_t)h->ll - h->sl;
-    return std::min<int64_t>(want, D);
+    const int64_t cap = std::min<int64_t>(want, D / unit);
+    int lg = 0;
+    while ((int64_t)2 << lg <= cap) ++lg;
+    return lg;
 }
 
 int lfg_fill(Handle* h, void* dst, int64_t n, int mode, cudaStream_t st)
@@ -473,10 +495,12 @@ int lfg_fill(Handle* h, void* dst, int64_t n, int mode, cudaStream_t st)
     a.sl = h->sl;
     a.base = h->pos;
     a.n_units = n;
-    int64_t C = max_chunk_positions(h, 2048) & ~(int64_t)3;
+    a.logC = log2_chunk(h, 2048, 1);
+    const int64_t C = (int64_t)1 << a.logC;
     a.C = C;
     a.Cpos = C;
     a.total_chunks = (n + C - 1) / C;
+    if (a.total_chunks >= ((int64_t)1 << 31)) return fail(GBRNG_EINVAL, "fill too large for one call");
     a.out = dst;
     int64_t G = 0;
     if (mode == LFG_U32)
@@ -533,14 +557,16 @@ int lfg_ld(const ld_system* s, int64_t n_steps, int init, ld_stats* out, cudaStr
     a.base = h->pos;
     a.n_units = s->n;
     a.n_steps = init ? 2 : n_steps;
-    int64_t C = max_chunk_positions(h, 4 * 512) / 4;   // oscillators per chunk
-    C &= ~(int64_t)3;
-    if (C < 4) C = 4;
-    if (C > s->n) C = (s->n + 3) & ~(int64_t)3;
+    a.logC = log2_chunk(h, 512, 4);                   // oscillators per chunk
+    const int64_t C = (int64_t)1 << a.logC;
     a.C = C;
     a.Cpos = 4 * C;
     a.M = (s->n + C - 1) / C;
+    a.per_step = 4 * s->n;
+    a.inv_per_step = 1.0 / (double)a.per_step;
     a.total_chunks = a.M * a.n_steps;
+    if (a.total_chunks >= ((int64_t)1 << 31))
+        return fail(GBRNG_EINVAL, "split runs of more than 2^31 chunks (N x steps / %lld)", (long long)C);
     a.x = s->x;
     a.v = s->v;
     a.Kper = s->K_per;

@@ -54,11 +54,14 @@ def test_batched_equals_per_system(G, kind, tune):
     sa = G.ld_run_batched(a, steps, tune=tune)
     sb = [G.ld_run(s, steps) for s in b]
     assert_same(G, a, b)
-    # statistics: same per-oscillator values summed in another order (and, when
-    # the steps are split over launches, Kahan sums restarted per launch)
+    # statistics: the same per-oscillator values summed in another order; when
+    # the steps are split over launches the binary32 Kahan sum of each
+    # oscillator's energy restarts per launch (a few ulp of binary32)
+    split = tune is None or tune[2] > 0
+    rtol = 1e-7 if split else 1e-12
     for x, y in zip(sa, sb):
         for k in ("sum_x2", "sum_v2", "sum_xv", "energy_time_avg"):
-            assert math.isclose(x[k], y[k], rel_tol=1e-9, abs_tol=1e-9), (k, x[k], y[k])
+            assert math.isclose(x[k], y[k], rel_tol=rtol, abs_tol=1e-9), (k, x[k], y[k])
         assert x["steps"] == steps
 
 

@@ -376,3 +376,12 @@ def test_fill_layout_per_thread():
     assert [int(v) for v in out] == exp
     assert np.array_equal(a.state[:3], c.state[:3])          # drew 3 times
     assert not np.array_equal(a.state[3:], c.state[3:])      # drew 2 times
+
+
+@pytest.mark.parametrize("kind", ["taus", "ran2"])
+def test_seed_selected_streams(kind):
+    """Seeding a list of stream indices gives the rows a full seeding gives."""
+    full = oracle.Gen(kind, 17, 300)
+    idx = [0, 5, 299, 123]
+    sub = oracle.Gen.streams(kind, 17, idx)
+    assert np.array_equal(sub.state, full.state[idx])
