@@ -7,7 +7,8 @@ workload (10^6 independent 3-D oscillators, the paper's Sec. IV test shape):
     Ran2, Lagged Fibonacci on the last Table I row), seeding excluded;
   - stand-alone fills of 2^30 uniform and 2^30 normal binary32 numbers per
     generator;
-  - the batched and adjoint paths when the library provides them.
+  - 512 uneven systems (N log-uniform in [1e2, 1e5]) x 5000 steps in one
+    batched graph launch, and the adjoint of 1e5 oscillators x 1e4 steps.
 value = oscillator-steps advanced per second over the whole step (fills
 count toward the time, not the oscillator-steps).  Inputs stay resident in
 HBM; the L2 (126 MB) is flushed by a 256 MiB write before every timed part.
@@ -32,6 +33,8 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+from paper_1003_1123_gb300 import workloads as W  # noqa: E402  (seeded inputs only)
+
 N_OSC = 10**6
 LD_STEPS = 10**4
 FILL_N = 2**30
@@ -39,6 +42,11 @@ SEED = 2024
 KINDS = ("taus", "ran2", "lagfib")
 L2_FLUSH_BYTES = 256 << 20
 PARAMS = dict(K=1.0, m=1.0, gamma=0.5, kT=1.0, dt=0.01)
+BATCH_SYSTEMS, BATCH_STEPS = 512, 5000
+ADJ_N, ADJ_STEPS, ADJ_CKPT = 10**5, 10**4, 100
+WORKLOAD = ("N=1e6 3-D oscillators x 1e4 fused steps per generator (Taus, Ran2, Lagged "
+            "Fibonacci row 9) + 2^30 uniform and 2^30 normal fills per generator + 512 uneven "
+            "systems (N 1e2..1e5) x 5000 batched steps + adjoint of 1e5 oscillators x 1e4 steps")
 
 # Integer operations per oscillator-step that the generators themselves
 # require (four draws): Hybrid Taus 4 x (3 x 5 shift/logic + 1 LCG multiply-
@@ -136,6 +144,23 @@ class Workload:
         self.fill_rngs = {k: G.rng_init(k, seed + 7, N_OSC) for k in KINDS}
         self.out = torch.empty(FILL_N, dtype=torch.float32, device="cuda")
         self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        # batched: 512 uneven systems (Hybrid Taus), one graph launch per call
+        self.batch = []
+        for i, sp in enumerate(W.batched_systems(BATCH_SYSTEMS, seed=1234 + rank)):
+            r = G.rng_init("taus", sp["seed"], sp["n"])
+            x = torch.zeros((sp["n"], 3), dtype=torch.float32, device="cuda")
+            s = G.LdSystem(r, x, torch.zeros_like(x), K=sp["K"], m=sp["m"], gamma=sp["gamma"],
+                           kT=sp["kT"], dt=sp["dt"])
+            G.ld_init_equilibrium(s)
+            self.batch.append(s)
+        self.batch_osc = sum(s.n for s in self.batch)
+        # adjoint: 1e5 oscillators, K per oscillator, checkpoints every 100 steps
+        ra = G.rng_init("taus", seed + 11, ADJ_N)
+        xa = torch.zeros((ADJ_N, 3), dtype=torch.float32, device="cuda")
+        self.adj = G.LdSystem(ra, xa, torch.zeros_like(xa), K_per=torch.ones(ADJ_N, device="cuda"),
+                              **{k: v for k, v in PARAMS.items() if k != "K"})
+        G.ld_init_equilibrium(self.adj)
+        self.dK = torch.empty(ADJ_N, dtype=torch.float32, device="cuda")
         torch.cuda.synchronize()
 
     def parts(self):
@@ -150,6 +175,10 @@ class Workload:
                         lambda r=r: G.rng_fill_uniform(r, FILL_N, out=self.out)))
             out.append((f"fill_normal_{kind}", 0,
                         lambda r=r: G.rng_fill_normal(r, FILL_N, out=self.out)))
+        out.append(("batched_taus", self.batch_osc * BATCH_STEPS,
+                    lambda: G.ld_run_batched(self.batch, BATCH_STEPS)))
+        out.append(("adjoint_taus", ADJ_N * ADJ_STEPS,
+                    lambda: G.ld_backward(self.adj, ADJ_STEPS, ADJ_CKPT, dK=self.dK)))
         return out
 
     def step(self, parts, events):
@@ -209,7 +238,8 @@ def run_gpu(args, rank, world, dist):
     peaks, peak_src = load_peaks()
     dom = max(part_ms, key=part_ms.get)
     dom_ms = part_ms[dom] / args.steps
-    roof = roofline(dom, dom_ms, peaks, peak_src, clk)
+    units_of = {name: units for name, units, _ in parts}
+    roof = roofline(dom, dom_ms, units_of[dom], peaks, peak_src, clk)
     per_part = {name: {"ms": round(part_ms[name] / args.steps, 4)} for name in part_ms}
     for name, units, _ in parts:
         if units:
@@ -217,6 +247,7 @@ def run_gpu(args, rank, world, dist):
         else:
             per_part[name]["numbers_per_s"] = FILL_N / (part_ms[name] / args.steps / 1e3)
             per_part[name]["GBps"] = FILL_N * 4 / (part_ms[name] / args.steps / 1e3) / 1e9
+    extras = compare_paths(wl, G, torch, part_ms, args.steps)
 
     line = {
         "metric": "oscillator-steps/s (fused LD+RNG, all generators, whole hot path)",
@@ -231,9 +262,10 @@ def run_gpu(args, rank, world, dist):
         "vs_baseline": None,
         "dtype": "f32+u32",
         "data": "synthetic (seeded oscillators; equilibrium start)",
-        "config": {"workload": "N=1e6 3-D oscillators x 1e4 fused steps per generator "
-                               "(Taus, Ran2, Lagged Fibonacci row 9) + 2^30 uniform and "
-                               "2^30 normal fills per generator",
+        "config": {"workload": WORKLOAD,
+                   "batched": {"systems": BATCH_SYSTEMS, "oscillators": wl.batch_osc,
+                               "steps": BATCH_STEPS},
+                   "adjoint": {"n": ADJ_N, "steps": ADJ_STEPS, "checkpoint_every": ADJ_CKPT},
                    "n_oscillators": N_OSC, "ld_steps": LD_STEPS, "fill_numbers": FILL_N,
                    "params": PARAMS, "l2": "flushed (256 MiB write) before every part",
                    "parallelism": f"replicas x{world} (independent seeds, no collective)"},
@@ -242,6 +274,7 @@ def run_gpu(args, rank, world, dist):
         "e2e": e2e,
         "roofline": roof,
         "parts": per_part,
+        "comparisons": extras,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(parts, part_ms, args.steps)
@@ -253,8 +286,36 @@ def gpu_launches(parts, steps):
     run plus the statistics finisher, one kernel per fill."""
     n = 0
     for name, _, _ in parts:
-        n += 2 if name.startswith("ld_") else 1
+        if name.startswith("ld_") or name.startswith("adjoint"):
+            n += 2                  # persistent kernel + statistics finisher
+        elif name.startswith("batched"):
+            n += 2                  # graph: one persistent launch + per-system reduction
+        else:
+            n += 1
     return n * steps
+
+
+def compare_paths(wl, G, torch, part_ms, steps):
+    """Outside the timed region: the batched systems run one ld_run each (the
+    per-system alternative the batched graph replaces), and a plain forward
+    run of the adjoint system (the adjoint's cost relative to a forward)."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in wl.batch:
+        G.ld_run(s, BATCH_STEPS, stats=False)
+    torch.cuda.synchronize()
+    per_system_ms = 1e3 * (time.perf_counter() - t0)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    G.ld_run(wl.adj, ADJ_STEPS)
+    b.record()
+    torch.cuda.synchronize()
+    fwd_ms = a.elapsed_time(b)
+    batched_ms = part_ms["batched_taus"] / steps
+    adj_ms = part_ms["adjoint_taus"] / steps
+    return {"batched_ms": batched_ms, "per_system_launches_ms": per_system_ms,
+            "batched_speedup": per_system_ms / batched_ms,
+            "adjoint_ms": adj_ms, "forward_ms": fwd_ms, "adjoint_over_forward": adj_ms / fwd_ms}
 
 
 def run_e2e(args, wl, parts, G, torch):
@@ -264,6 +325,9 @@ def run_e2e(args, wl, parts, G, torch):
     host = {}
     for kind, s in wl.systems.items():
         host[kind] = (s.x.cpu().pin_memory(), s.v.cpu().pin_memory())
+    host_batch = [(s.x.cpu().pin_memory(), s.v.cpu().pin_memory()) for s in wl.batch]
+    host_adj = (wl.adj.x.cpu().pin_memory(), wl.adj.v.cpu().pin_memory(),
+                torch.empty(ADJ_N, dtype=torch.float32).pin_memory())
     probe = torch.empty(1024, dtype=torch.float32).pin_memory()
     h2d = d2h = 0
     torch.cuda.synchronize()
@@ -271,7 +335,25 @@ def run_e2e(args, wl, parts, G, torch):
     for _ in range(args.steps):
         h2d = d2h = 0
         for name, _, fn in parts:
-            if name.startswith("ld_"):
+            if name.startswith("batched"):
+                for s, (hx, hv) in zip(wl.batch, host_batch):
+                    s.x.copy_(hx, non_blocking=True)
+                    s.v.copy_(hv, non_blocking=True)
+                    h2d += 2 * hx.numel() * 4
+                fn()
+                for s, (hx, hv) in zip(wl.batch, host_batch):
+                    hx.copy_(s.x, non_blocking=True)
+                    hv.copy_(s.v, non_blocking=True)
+                    d2h += 2 * hx.numel() * 4 + 40
+            elif name.startswith("adjoint"):
+                hx, hv, hd = host_adj
+                wl.adj.x.copy_(hx, non_blocking=True)
+                wl.adj.v.copy_(hv, non_blocking=True)
+                h2d += 2 * hx.numel() * 4
+                fn()
+                hd.copy_(wl.dK, non_blocking=True)
+                d2h += hd.numel() * 4 + 24
+            elif name.startswith("ld_"):
                 kind = name[3:]
                 s = wl.systems[kind]
                 hx, hv = host[kind]
@@ -293,23 +375,30 @@ def run_e2e(args, wl, parts, G, torch):
             "d2h_bytes_per_step": d2h}
 
 
-def roofline(part, ms, peaks, src, clk):
+def roofline(part, ms, units, peaks, src, clk):
+    """Roofline of one part: fills against the measured HBM copy bandwidth (4 B
+    per number); Lagged Fibonacci fused steps against HBM with 96 algorithmic
+    bytes per oscillator-step; Taus/Ran2 fused, batched and adjoint work
+    against the INT32 lanes (algorithmic integer ops of the generator: 72 or 52
+    per oscillator-step; the adjoint draws every number twice)."""
     mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     kind = part.split("_")[-1]
+    sec = ms / 1e3
     if part.startswith("fill_"):
-        achieved = FILL_N * FILL_BYTES_PER_NUMBER / (ms / 1e3) / 1e9
+        achieved = FILL_N * FILL_BYTES_PER_NUMBER / sec / 1e9
         peak = peaks["hbm_gbs"]
         return {"kernel": part, "bound": "hbm", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": f"{src} hbm_gbs (copy bandwidth)"}
     if kind == "lagfib":
-        achieved = N_OSC * LD_STEPS * LFG_BYTES_PER_OSC_STEP / (ms / 1e3) / 1e9
+        achieved = units * LFG_BYTES_PER_OSC_STEP / sec / 1e9
         peak = peaks["hbm_gbs"]
         return {"kernel": part, "bound": "hbm", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": None,
                 "peak_source": f"{src} hbm_gbs; algorithmic 96 B per oscillator-step"}
-    ops = INT_OPS_PER_OSC_STEP[kind] * N_OSC * LD_STEPS
-    achieved = ops / (ms / 1e3) / 1e12
+    draws = 2 if part.startswith("adjoint") else 1
+    ops = draws * INT_OPS_PER_OSC_STEP[kind] * units
+    achieved = ops / sec / 1e12
     peak = SMS * INT32_LANES_PER_SM * mhz * 1e6 / 1e12
     return {"kernel": part, "bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
@@ -348,29 +437,47 @@ def _oracle_rates(budget_scale=1.0):
         t0 = time.perf_counter()
         g.fill_normal(nf)
         rates[f"fill_normal_{kind}"] = nf / (time.perf_counter() - t0)
-    np.asarray(0)
+    # batched systems run the same per-oscillator arithmetic as a Taus system
+    rates["batched_taus"] = rates["ld_taus"]
+    na, sa = max(8, int(200 * budget_scale)), 1000
+    g = oracle.Gen("taus", SEED + 11, na)
+    x, v = oracle.ld_init_eq_f64(g, na, p)
+    t0 = time.perf_counter()
+    oracle.ld_adjoint_f64(g, x, v, p, sa, Kper=np.ones(na))
+    rates["adjoint_taus"] = na * sa / (time.perf_counter() - t0)
     return rates
 
 
+def _step_units():
+    batch_osc = sum(sp["n"] for sp in W.batched_systems(BATCH_SYSTEMS, seed=1234))
+    units = {f"ld_{k}": N_OSC * LD_STEPS for k in KINDS}
+    units.update({f"fill_{m}_{k}": FILL_N for k in KINDS for m in ("uniform", "normal")})
+    units["batched_taus"] = batch_osc * BATCH_STEPS
+    units["adjoint_taus"] = ADJ_N * ADJ_STEPS
+    return units
+
+
+def _step_osc_steps(units):
+    return sum(u for name, u in units.items() if not name.startswith("fill_"))
+
+
 def _cpu_step_seconds(rates):
-    sec = 0.0
-    for name, r in rates.items():
-        units = N_OSC * LD_STEPS if name.startswith("ld_") else FILL_N
-        sec += units / r
-    return sec
+    units = _step_units()
+    return sum(units[name] / r for name, r in rates.items())
 
 
 def _sample_text(scale):
     return (f"per generator: Taus/Ran2 {int(20000 * scale)} oscillators x 100 steps, Lagged "
             f"Fibonacci all 1e6 oscillators x {max(1, int(2 * scale))} steps, "
-            f"{int(2e6 * scale)} uniform + {int(2e6 * scale)} normal fill numbers; "
-            f"extrapolated per unit to the full step")
+            f"{int(2e6 * scale)} uniform + {int(2e6 * scale)} normal fill numbers, "
+            f"FP64 adjoint of {max(8, int(200 * scale))} oscillators x 1000 steps (batched "
+            f"systems at the Taus rate); extrapolated per unit to the full step")
 
 
 def cpu_baseline(parts, part_ms, steps):
     rates = _oracle_rates(1.0)
     sec = _cpu_step_seconds(rates)
-    return {"value": N_OSC * LD_STEPS * 3 / sec, "unit": "oscillator-steps/s", "cores": 1,
+    return {"value": _step_osc_steps(_step_units()) / sec, "unit": "oscillator-steps/s", "cores": 1,
             "kind": "oracle", "sample": _sample_text(1.0),
             "parts": {k: v for k, v in rates.items()}}
 
@@ -390,7 +497,7 @@ def run_reference(args, world):
         secs.append(_cpu_step_seconds(rates))
     wall = time.perf_counter() - t0
     ms_per_step = 1e3 * statistics.mean(secs)
-    value = N_OSC * LD_STEPS * 3 / (ms_per_step / 1e3)
+    value = _step_osc_steps(_step_units()) / (ms_per_step / 1e3)
     return {
         "impl": "reference",
         "metric": "oscillator-steps/s (fused LD+RNG, all generators, whole hot path)",
@@ -398,9 +505,7 @@ def run_reference(args, world):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+u32",
         "data": "synthetic (seeded oscillators; equilibrium start)",
-        "config": {"workload": "N=1e6 3-D oscillators x 1e4 fused steps per generator "
-                               "(Taus, Ran2, Lagged Fibonacci row 9) + 2^30 uniform and "
-                               "2^30 normal fills per generator", "timed_wall_s": wall},
+        "config": {"workload": WORKLOAD, "timed_wall_s": wall},
         "cpu_baseline": {"value": value, "unit": "oscillator-steps/s", "cores": 1,
                          "kind": "oracle", "sample": _sample_text(scale)},
         "e2e": {"value": value, "unit": "oscillator-steps/s", "h2d_bytes_per_step": 0,

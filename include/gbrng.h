@@ -24,7 +24,7 @@
  *    state in rng_init* and frees everything in rng_destroy.
  *  - A handle is not thread-safe; calls on one handle must not overlap.
  *  - Device errors map to GBRNG_ECUDA; a device-side wait that exceeded its
- *    limit (Lagged Fibonacci chunk flags) maps to GBRNG_ETIMEOUT, after which
+ *    limit (Lagged Fibonacci grid barrier) maps to GBRNG_ETIMEOUT, after which
  *    the handle's state is undefined (rng_set_state or a new handle recovers).
  */
 #ifndef GBRNG_H
@@ -133,14 +133,16 @@ int rng_get_state(gbrng_t rng, void* host, size_t bytes);
 int rng_set_state(gbrng_t rng, const void* host, size_t bytes);
 
 /* Bound (nanoseconds, default 2e9) on every device-side spin wait of the
- * library (Lagged Fibonacci chunk flags).  A wait that runs out makes the
- * kernel record GBRNG_ETIMEOUT and return.  Process-wide. */
+ * library (the Lagged Fibonacci grid barrier between rounds).  A wait that
+ * runs out makes the kernel record GBRNG_ETIMEOUT and return; the generator
+ * position is then not advanced and its ring contents are unspecified (reseed
+ * or set_state before further use).  Process-wide. */
 int rng_set_wait_limit_ns(uint64_t ns);
 
 /* Test hook for the bounded waits: from the next Lagged Fibonacci launch on,
- * the CTA that processes launch-relative chunk `chunk` stops publishing its
- * progress, so every chunk that depends on it waits until the limit runs out
- * and the call returns GBRNG_ETIMEOUT (no fault, no trap).  -1 switches the
+ * CTA number `chunk` modulo the launch's grid size never arrives at the grid
+ * barrier, so every CTA's wait runs out after the limit and a launch of more
+ * than one round returns GBRNG_ETIMEOUT (no fault, no trap).  -1 switches the
  * hook off (the default).  Process-wide. */
 int gbrng_test_stall_chunk(int64_t chunk);
 

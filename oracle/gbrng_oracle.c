@@ -93,7 +93,7 @@ void or_taus_seed(uint64_t seed, int64_t n, uint32_t* st)
 
 /* Schrage's factorisation a*x mod m = a*(x mod q) - r*(x div q) (+m if < 0)
  * for 0 < x < m; q = m div a and r = m mod a are derived here, not tabulated.
- * which = 0: (a1, m1); which = 1: (a2, m2).  Algorithm 2, lines 21-28. */
+ * which = 0: (a1, m1); which = 1: (a2, m2).  Schrage step of Algorithm 2. */
 int32_t or_ran2_schrage(int32_t x, int which)
 {
     const int32_t m = which ? R2_M2 : R2_M1;
@@ -105,7 +105,7 @@ int32_t or_ran2_schrage(int32_t x, int which)
     return y;
 }
 
-/* Algorithm 2, lines 1-14, for one stream, plus reading R5 (iy = iv[0]). */
+/* Seeding part of Algorithm 2 for one stream, plus reading R5 (iy = iv[0]). */
 static void ran2_init_one(int32_t idum, int32_t* st)
 {
     int32_t* iv = st + 3;
@@ -182,7 +182,7 @@ int or_lfg_default_row(int64_t n_threads)
  * Generators
  * ---------------------------------------------------------------------- */
 
-/* One Tausworthe step of Algorithm 1 (lines 6-11) with the triples of R1. */
+/* One Tausworthe word step of Algorithm 1 with the triples of R1. */
 uint32_t or_taus_component(uint32_t y, int which)
 {
     static const int s1[3] = {13, 2, 3}, s2[3] = {19, 25, 11}, s3[3] = {12, 4, 17};
@@ -191,7 +191,7 @@ uint32_t or_taus_component(uint32_t y, int which)
     return ((y & c[which]) << s3[which]) ^ b;
 }
 
-/* Algorithm 1, lines 6-13: advance the three Tausworthe words and the LCG
+/* Algorithm 1: advance the three Tausworthe words and the LCG
  * (a=1664525, c=1013904223), output the xor of the four new words. */
 uint32_t or_taus_next(uint32_t* y)
 {
@@ -202,7 +202,7 @@ uint32_t or_taus_next(uint32_t* y)
     return y[0] ^ y[1] ^ y[2] ^ y[3];
 }
 
-/* Algorithm 2, lines 21-37: returns the integer iy in [1, m1-1]. */
+/* Draw of Algorithm 2: returns the integer iy in [1, m1-1]. */
 int32_t or_ran2_next(int32_t* st)
 {
     int32_t* iv = st + 3;
@@ -216,7 +216,7 @@ int32_t or_ran2_next(int32_t* st)
     return iy;
 }
 
-/* Algorithm 3, lines 6-10, for the next position p = pos. */
+/* Recurrence of Algorithm 3 for the next position p = pos. */
 uint32_t or_lfg_next(or_gen* g)
 {
     uint32_t* x = (uint32_t*)g->state;
@@ -235,7 +235,7 @@ uint32_t or_lfg_next(or_gen* g)
 
 float or_u01_f32(uint32_t raw)
 {
-    return (float)raw * 0x1p-32f;        /* mult of Algorithm 1, line 12 */
+    return (float)raw * 0x1p-32f;        /* mult of Algorithm 1 */
 }
 
 double or_open01(uint32_t raw)

@@ -50,7 +50,7 @@ constexpr int32_t kR2Ndiv = 1 + kR2Imm1 / 32;
 static_assert(kR2Q1 == kR2M1 / kR2A1 && kR2R1 == kR2M1 % kR2A1, "Schrage constants");
 static_assert(kR2Q2 == kR2M2 / kR2A2 && kR2R2 == kR2M2 % kR2A2, "Schrage constants");
 
-// a*x mod m for 0 < x < m (Algorithm 2, lines 21-28).  x is positive, so the
+// a*x mod m for 0 < x < m (Schrage step of Algorithm 2).  x is positive, so the
 // quotient uses unsigned division by a constant (a multiply-high).
 template <int32_t A, int32_t M, int32_t Q, int32_t R>
 __host__ __device__ __forceinline__ int32_t schrage(int32_t x)
@@ -94,11 +94,12 @@ __device__ __forceinline__ float u01_from_ran2(int32_t iy)
     return fminf(__fmul_rn(am, __int2float_rn(iy)), rnmx);
 }
 
-// Open-interval Box-Muller input ((raw >> 9) + 1/2) * 2^-23: the 24-bit odd
-// integer (raw >> 8) | 1 scaled by 2^-24, exact in binary32.
+// Open-interval Box-Muller input ((raw >> 9) + 1/2) * 2^-23, exact in
+// binary32: the bits 0x3f800000 + (raw >> 9) are 1 + k 2^-23 (k = raw >> 9),
+// and subtracting 1 - 2^-24 leaves k 2^-23 + 2^-24 with no rounding.
 __device__ __forceinline__ float open01_from_u32(uint32_t raw)
 {
-    return __fmul_rn(__uint2float_rn((raw >> 8) | 1u), 0x1p-24f);
+    return __fsub_rn(__uint_as_float(0x3f800000u + (raw >> 9)), 0x1.fffffep-1f);
 }
 
 // ---------------------------------------------------------------- Box-Muller
@@ -284,17 +285,19 @@ __device__ __forceinline__ uint64_t global_ns()
     return t;
 }
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p)
+__device__ __forceinline__ void red_release_add_u32(uint32_t* p, uint32_t v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p)
 {
     uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v)
-{
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
 
 __device__ __forceinline__ int ld_volatile_i32(const int* p)
 {

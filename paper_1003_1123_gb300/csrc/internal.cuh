@@ -42,7 +42,7 @@ struct Handle {
     int32_t* r2 = nullptr;     // [35][n]: idum, idum2, iy, iv[0..31]
 
     // Lagged Fibonacci: the sequence value at position p lives in
-    // ring[p & ring_mask]; ring size R = ring_mask + 1 >= ll + 2 * max chunk.
+    // ring[p & ring_mask]; ring size R = ring_mask + 1 >= 2 ll + 2 (ll - sl).
     int row = -1;
     int32_t sl = 0, ll = 0;
     uint32_t ring_mask = 0;
@@ -50,7 +50,7 @@ struct Handle {
     int64_t pos = 0;           // next position to generate
 
     // scratch owned by the handle
-    uint32_t* progress = nullptr;   // per-CTA chunk counters (LFG)
+    uint32_t* progress = nullptr;   // grid-barrier arrival counter (LFG)
     int64_t progress_cap = 0;
     int* dstatus = nullptr;         // device status word
     double* partials = nullptr;     // per-block reduction partials

@@ -117,7 +117,7 @@ __global__ void taus_seed_kernel(uint64_t seed, int64_t n, uint4* st)
     st[s] = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// Algorithm 2, lines 2-13, per stream: idum2 <- idum, NTAB+8 Schrage steps,
+// Seeding part of Algorithm 2, per stream: idum2 <- idum, NTAB+8 Schrage steps,
 // the last NTAB fill iv[]; iy starts as iv[0].  Layout [35][n].
 __global__ void ran2_seed_kernel(uint64_t seed, int64_t n, int32_t* st)
 {
@@ -171,10 +171,13 @@ static int alloc_state(Handle* h)
     } else if (h->kind == GBRNG_RAN2) {
         e = cudaMalloc(&h->r2, sizeof(int32_t) * 35 * h->n);
     } else {
-        // ring size: power of two >= 2 ll + 16384 words (the leap reads back
-        // to p - 2 ll; the margin keeps overwritten values far behind readers)
+        // ring size: power of two >= 2 ll + 2 D + 16384 words.  The leap reads
+        // back to p - 2 ll, and a round of W <= 2 D positions overwrites
+        // positions p - R, so R - 2 ll >= 2 D lets every round take its full
+        // width (the margin keeps overwritten values well behind readers).
+        const uint64_t D = (uint64_t)(h->ll - h->sl);
         uint64_t R = 1;
-        while (R < 2 * (uint64_t)h->ll + 16384u) R <<= 1;
+        while (R < 2 * (uint64_t)h->ll + 2 * D + 16384u) R <<= 1;
         h->ring_mask = (uint32_t)(R - 1);
         e = cudaMalloc(&h->ring, sizeof(uint32_t) * R);
     }

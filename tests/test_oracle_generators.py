@@ -43,7 +43,7 @@ def test_taus_component_matches_bit_recurrence(which, k, q, s):
     """Eq. 2 defines the Tausworthe bits by a linear recurrence mod 2; with the
     trinomial z^k - z^q - 1 it reads b_n = b_{n-(k-q)} xor b_{n-k}, and word n
     holds bits b_{ns} .. b_{ns+31} (most significant first).  The fast word
-    step of Algorithm 1 (lines 6-11) must reproduce it for every n >= 1."""
+    word step of Algorithm 1 must reproduce it for every n >= 1."""
     rng = np.random.default_rng(7 + which)
     for _ in range(4):
         a0 = int(rng.integers(0, 2**32))
@@ -89,7 +89,7 @@ def test_taus_combined_period_claim():
 
 
 def test_taus_output_advances_before_output():
-    """Algorithm 1: words are advanced first (lines 6-12), then line 13 outputs
+    """Algorithm 1: words are advanced first, then the output is
     their xor.  From the all-zero Tausworthe words the output is the LCG word."""
     y = np.array([0, 0, 0, 5], np.uint32)
     out = oracle.taus_next(y)
@@ -101,7 +101,7 @@ M1, A1, M2, A2 = 2147483563, 40014, 2147483399, 40692
 
 
 def test_ran2_schrage_equals_modular_product():
-    """Algorithm 2 lines 21-28 compute a*x mod m by Schrage's factorisation."""
+    """Algorithm 2 computes a*x mod m by Schrage's factorisation."""
     rng = np.random.default_rng(3)
     for which, (m, a) in enumerate([(M1, A1), (M2, A2)]):
         xs = list(rng.integers(1, m, 2000)) + [1, 2, m - 1, m - 2, m // a, m // a + 1]
@@ -157,7 +157,7 @@ def test_ran2_output_range_and_shuffle_conservation():
 
 
 def test_ran2_init_warmup():
-    """Algorithm 2 lines 2-13: idum2 = seed, NTAB+8 Schrage steps, the last NTAB
+    """Algorithm 2's seeding: idum2 = seed, NTAB+8 Schrage steps, the last NTAB
     stored with iv[j] at j = NTAB-1 .. 0; iy starts as iv[0] (reading)."""
     g = oracle.Gen("ran2", 5, 2)
     for s in range(2):
@@ -306,7 +306,7 @@ def test_lfg_default_row_selection():
 
 # ------------------------------------------------------------- conversions
 def test_uniform_conversions_ranges():
-    """Algorithm 1 line 13: u = mult * raw with mult = 2^-32 lies in [0, 1]
+    """Algorithm 1's conversion: u = mult * raw with mult = 2^-32 lies in [0, 1]
     (1.0 from raw >= 2^32-128 after rounding); the Box-Muller map is open."""
     assert oracle.u01_f32(0) == 0.0
     assert oracle.u01_f32(2**32 - 1) == 1.0
