@@ -49,14 +49,20 @@ WORKLOAD = ("N=1e6 3-D oscillators x 1e4 fused steps per generator (Taus, Ran2, 
             "systems (N 1e2..1e5) x 5000 batched steps + adjoint of 1e5 oscillators x 1e4 steps")
 
 # Integer operations per oscillator-step that the generators themselves
-# require (four draws): Hybrid Taus 4 x (3 x 5 shift/logic + 1 LCG multiply-
-# add + 2 combining xors) = 72; Ran2 4 x (2 Schrage steps of 5 (multiply-high
-# quotient, two multiply-adds, compare-add) + table index, subtract, wrap) = 52.
-INT_OPS_PER_OSC_STEP = {"taus": 72, "ran2": 52}
-# Algorithmic bytes per oscillator-step of the Lagged Fibonacci fused step:
-# four ring values (2 lag reads + 1 write each, 4 B) = 48 B, plus x, v read and
-# written (24 + 24 B) = 96 B.
-LFG_BYTES_PER_OSC_STEP = 96
+# require (four draws), one per operator of the algorithm:
+#   Hybrid Taus: 3 components x 6 shift/logic ops + LCG multiply and add (2)
+#                + 3 combining xors = 23 per draw -> 92;
+#   Ran2: 2 Schrage steps x 8 (quotient, 3 multiplies, 2 subtracts, compare,
+#         add) + shuffle (index quotient, subtract, compare, add, table load
+#         and store) 6 = 22 per draw -> 88.
+INT_OPS_PER_OSC_STEP = {"taus": 92, "ran2": 88}
+# Algorithmic bytes per oscillator-step of the Lagged Fibonacci fused step at
+# 1e6 oscillators: four ring values, each 2 lag reads + 1 write of 4 B = 48 B
+# (x and v stay in shared memory for the whole launch).  The ring (64 MiB for
+# the last Table I row) stays in L2, so the bound is L2 bandwidth, measured
+# below as a device-to-device copy of 2 x 32 MiB that stays L2-resident.
+LFG_BYTES_PER_OSC_STEP = 48
+L2_COPY_BYTES = 32 << 20
 FILL_BYTES_PER_NUMBER = 4
 
 
@@ -239,8 +245,12 @@ def run_gpu(args, rank, world, dist):
     dom = max(part_ms, key=part_ms.get)
     dom_ms = part_ms[dom] / args.steps
     units_of = {name: units for name, units, _ in parts}
-    roof = roofline(dom, dom_ms, units_of[dom], peaks, peak_src, clk)
+    l2_gbs = measure_l2_copy_gbs(torch)
+    roof = roofline(dom, dom_ms, units_of[dom], peaks, peak_src, clk, l2_gbs)
     per_part = {name: {"ms": round(part_ms[name] / args.steps, 4)} for name in part_ms}
+    for name in part_ms:
+        r = roofline(name, part_ms[name] / args.steps, units_of[name], peaks, peak_src, clk, l2_gbs)
+        per_part[name]["roofline"] = {k: r[k] for k in ("bound", "achieved", "unit", "frac")}
     for name, units, _ in parts:
         if units:
             per_part[name]["osc_steps_per_s"] = units / (part_ms[name] / args.steps / 1e3)
@@ -375,12 +385,30 @@ def run_e2e(args, wl, parts, G, torch):
             "d2h_bytes_per_step": d2h}
 
 
-def roofline(part, ms, units, peaks, src, clk):
+def measure_l2_copy_gbs(torch):
+    """L2-resident copy bandwidth: src and dst of 32 MiB each, 50 copies after
+    warm-up, bytes read + written over CUDA-event time."""
+    src = torch.empty(L2_COPY_BYTES // 4, dtype=torch.float32, device="cuda").fill_(1.0)
+    dst = torch.empty_like(src)
+    for _ in range(5):
+        dst.copy_(src)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(50):
+        dst.copy_(src)
+    e1.record()
+    torch.cuda.synchronize()
+    return 2 * L2_COPY_BYTES * 50 / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+
+def roofline(part, ms, units, peaks, src, clk, l2_gbs=None):
     """Roofline of one part: fills against the measured HBM copy bandwidth (4 B
-    per number); Lagged Fibonacci fused steps against HBM with 96 algorithmic
-    bytes per oscillator-step; Taus/Ran2 fused, batched and adjoint work
-    against the INT32 lanes (algorithmic integer ops of the generator: 72 or 52
-    per oscillator-step; the adjoint draws every number twice)."""
+    per number); Lagged Fibonacci fused steps against the L2 copy bandwidth
+    measured in this run (48 algorithmic bytes per oscillator-step); Taus/Ran2
+    fused, batched and adjoint work against the INT32 lanes (algorithmic
+    integer ops of the generator: 92 or 88 per oscillator-step; the adjoint
+    draws every number twice)."""
     mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     kind = part.split("_")[-1]
     sec = ms / 1e3
@@ -392,10 +420,10 @@ def roofline(part, ms, units, peaks, src, clk):
                 "peak_source": f"{src} hbm_gbs (copy bandwidth)"}
     if kind == "lagfib":
         achieved = units * LFG_BYTES_PER_OSC_STEP / sec / 1e9
-        peak = peaks["hbm_gbs"]
-        return {"kernel": part, "bound": "hbm", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": f"{src} hbm_gbs; algorithmic 96 B per oscillator-step"}
+        return {"kernel": part, "bound": "l2", "achieved": achieved, "peak": l2_gbs,
+                "unit": "GB/s", "frac": achieved / l2_gbs if l2_gbs else None, "traffic": None,
+                "peak_source": "L2-resident copy of 2 x 32 MiB measured in this run; "
+                               "algorithmic 48 B per oscillator-step"}
     draws = 2 if part.startswith("adjoint") else 1
     ops = draws * INT_OPS_PER_OSC_STEP[kind] * units
     achieved = ops / sec / 1e12
@@ -518,20 +546,21 @@ CASES = ("ld_taus", "ld_ran2", "ld_lagfib", "fill_uniform_taus", "fill_normal_ta
 
 
 def run_case(name: str):
-    """One small launch of one part (for profiler captures): fused runs use
-    2e5 oscillators x 200 steps, fills 2^28 numbers (1 GiB, larger than L2)."""
+    """Short launches of one part (for profiler captures): fused runs use the
+    bench's 1e6 oscillators x 100 steps (x and v: 24 MB), fills 2^28 numbers
+    (1 GiB, larger than L2)."""
     import torch
     from paper_1003_1123_gb300 import gbrng as G
     kind = name.split("_")[-1]
     if name.startswith("ld_"):
-        n = 200000
+        n = N_OSC
         r = G.rng_init(kind, SEED, n)
         x = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
         v = torch.zeros_like(x)
         s = G.LdSystem(r, x, v, **PARAMS)
         G.ld_init_equilibrium(s)
         for _ in range(2):
-            G.ld_run(s, 200)
+            G.ld_run(s, 100)
     else:
         r = G.rng_init(kind, SEED, N_OSC)
         out = torch.empty(2**28, dtype=torch.float32, device="cuda")

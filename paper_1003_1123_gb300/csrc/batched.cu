@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) batched_kernel(const SysDesc* __restrict_
         float x0[K], x1[K], x2[K], v0[K], v1[K], v2[K], ckx[K], hK[K];
         TausDraw td[K];
         Ran2Draw rd[K];
-        Kahan e[K];
+        EnergySum es[K];
 #pragma unroll
         for (int j = 0; j < K; ++j) {
             idx[j] = tile.first + tid + (int64_t)j * T;
@@ -81,16 +81,21 @@ __global__ void __launch_bounds__(256) batched_kernel(const SysDesc* __restrict_
                 for (int q = 0; q < 32; ++q) rd[j].tab[q * T + tid] = d.r2[(3 + q) * d.S + i];
             }
         }
-        for (int64_t t = 0; t < n_steps; ++t) {
+        for (int64_t t0 = 0; t0 < n_steps; t0 += kEnergyBlock) {
+            const int nb = (int)min((int64_t)kEnergyBlock, n_steps - t0);
+            for (int k = 0; k < nb; ++k) {
 #pragma unroll
-            for (int j = 0; j < K; ++j) {
-                float g0, g1, g2;
-                if (KIND == GBRNG_TAUS) td[j].normals3(g0, g1, g2); else rd[j].normals3(g0, g1, g2);
-                em_component(c.cdt, c.cva, ckx[j], c.cs, g0, x0[j], v0[j]);
-                em_component(c.cdt, c.cva, ckx[j], c.cs, g1, x1[j], v1[j]);
-                em_component(c.cdt, c.cva, ckx[j], c.cs, g2, x2[j], v2[j]);
-                e[j].add(energy3(hK[j], c.hm, x0[j], x1[j], x2[j], v0[j], v1[j], v2[j]));
+                for (int j = 0; j < K; ++j) {
+                    float g0, g1, g2;
+                    if (KIND == GBRNG_TAUS) td[j].normals3(g0, g1, g2); else rd[j].normals3(g0, g1, g2);
+                    em_component(c.cdt, c.cva, ckx[j], c.cs, g0, x0[j], v0[j]);
+                    em_component(c.cdt, c.cva, ckx[j], c.cs, g1, x1[j], v1[j]);
+                    em_component(c.cdt, c.cva, ckx[j], c.cs, g2, x2[j], v2[j]);
+                    es[j].add(x0[j], x1[j], x2[j], v0[j], v1[j], v2[j]);
+                }
             }
+#pragma unroll
+            for (int j = 0; j < K; ++j) es[j].flush();
         }
         double acc[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -111,7 +116,7 @@ __global__ void __launch_bounds__(256) batched_kernel(const SysDesc* __restrict_
             acc[0] += (double)x0[j] * x0[j] + (double)x1[j] * x1[j] + (double)x2[j] * x2[j];
             acc[1] += (double)v0[j] * v0[j] + (double)v1[j] * v1[j] + (double)v2[j] * v2[j];
             acc[2] += (double)x0[j] * v0[j] + (double)x1[j] * v1[j] + (double)x2[j] * v2[j];
-            acc[3] += e[j].value();
+            acc[3] += es[j].value(hK[j], c.hm);
         }
         block_reduce_sum<4>(acc, red);
         if (tid == 0) {

@@ -95,11 +95,23 @@ __device__ __forceinline__ float u01_from_ran2(int32_t iy)
 }
 
 // Open-interval Box-Muller input ((raw >> 9) + 1/2) * 2^-23, exact in
-// binary32: the bits 0x3f800000 + (raw >> 9) are 1 + k 2^-23 (k = raw >> 9),
+// binary32: the bits 0x3f800000 + (raw >> 9) are m = 1 + k 2^-23 (k = raw >> 9),
 // and subtracting 1 - 2^-24 leaves k 2^-23 + 2^-24 with no rounding.
+__device__ __forceinline__ float mant_from_u32(uint32_t raw)
+{
+    return __uint_as_float(0x3f800000u + (raw >> 9));
+}
+
 __device__ __forceinline__ float open01_from_u32(uint32_t raw)
 {
-    return __fsub_rn(__uint_as_float(0x3f800000u + (raw >> 9)), 0x1.fffffep-1f);
+    return __fsub_rn(mant_from_u32(raw), 0x1.fffffep-1f);
+}
+
+// 4u for the same u, in one fused step: 4m - (4 - 2^-22) = 4 k 2^-23 + 2^-22
+// is exact (below 4 the spacing is at most 2^-22).
+__device__ __forceinline__ float quarter_turns_from_u32(uint32_t raw)
+{
+    return __fmaf_rn(4.0f, mant_from_u32(raw), -0x1.fffffep+1f);
 }
 
 // ---------------------------------------------------------------- Box-Muller
@@ -107,45 +119,56 @@ __device__ __forceinline__ float open01_from_u32(uint32_t raw)
 // produce (u a positive normal binary32 below 1) with polynomial coefficients
 // fitted by fit_bm_coeffs.py; all within 2 ulp on those ranges.
 
+// R's coefficients in the variable g = -2f: c'_i = -c_i (-1)^i / 2^(i+1), exact
+// power-of-two rescalings of kLogR.
+__host__ __device__ constexpr float log_g_coef(int i)
+{
+    return -kLogR[i] * ((i & 1) ? -1.0f : 1.0f) / (float)(2 << i);
+}
+constexpr float kLogG[9] = {log_g_coef(0), log_g_coef(1), log_g_coef(2),
+                            log_g_coef(3), log_g_coef(4), log_g_coef(5),
+                            log_g_coef(6), log_g_coef(7), log_g_coef(8)};
+
 // -2 ln(u): u = 2^e m with m in [2/3, 4/3) (exponent split at the bits of 2/3),
 // f = m - 1 exact, ln m = f + f^2 R(f), ln u = e ln2 + ln m (ln2 in two parts).
+// Evaluated in g = -2f (exact), where every Estrin term is the f-form term
+// times an exact power of two, so the result equals -2 times the f-form ln u
+// bit for bit without the final multiply.
 __device__ __forceinline__ float neg2log(float u)
 {
     const int bits = __float_as_int(u);
     const int e = (bits - 0x3f2aaaab) >> 23;
-    const float f = __fsub_rn(__int_as_float(bits - (e << 23)), 1.0f);
-    const float f2 = __fmul_rn(f, f);
-    const float f4 = __fmul_rn(f2, f2);
-    // Estrin's scheme for R(f) of degree 8
-    const float p01 = __fmaf_rn(kLogR[1], f, kLogR[0]);
-    const float p23 = __fmaf_rn(kLogR[3], f, kLogR[2]);
-    const float p45 = __fmaf_rn(kLogR[5], f, kLogR[4]);
-    const float p67 = __fmaf_rn(kLogR[7], f, kLogR[6]);
-    const float p03 = __fmaf_rn(p23, f2, p01);
-    const float p47 = __fmaf_rn(p67, f2, p45);
-    const float p48 = __fmaf_rn(kLogR[8], f4, p47);
-    const float R = __fmaf_rn(p48, f4, p03);
-    const float lnm = __fmaf_rn(f2, R, f);
+    const float g = __fmaf_rn(__int_as_float(bits - (e << 23)), -2.0f, 2.0f);
+    const float g2 = __fmul_rn(g, g);
+    const float g4 = __fmul_rn(g2, g2);
+    const float p01 = __fmaf_rn(kLogG[1], g, kLogG[0]);
+    const float p23 = __fmaf_rn(kLogG[3], g, kLogG[2]);
+    const float p45 = __fmaf_rn(kLogG[5], g, kLogG[4]);
+    const float p67 = __fmaf_rn(kLogG[7], g, kLogG[6]);
+    const float p03 = __fmaf_rn(p23, g2, p01);
+    const float p47 = __fmaf_rn(p67, g2, p45);
+    const float p48 = __fmaf_rn(kLogG[8], g4, p47);
+    const float R = __fmaf_rn(p48, g4, p03);
+    const float l2m = __fmaf_rn(g2, R, g);
     const float ef = (float)e;
-    const float l = __fmaf_rn(ef, -0x1.05c610p-29f, __fmaf_rn(ef, 0x1.62e430p-1f, lnm));
-    return __fmul_rn(-2.0f, l);
+    return __fmaf_rn(ef, 0x1.05c610p-28f, __fmaf_rn(ef, -0x1.62e430p+0f, l2m));
 }
 
-// sqrt(y) for a positive normal y: reciprocal square root and one Newton step.
+// sqrt(y) for a positive normal y: the hardware approximation, within 1 ulp of
+// the correctly rounded root on the whole range the transform produces
+// ([2^-24, 64), checked exhaustively).
 __device__ __forceinline__ float sqrt_pos(float y)
 {
-    const float r = rsqrtf(y);
-    const float s = __fmul_rn(y, r);
-    const float d = __fmaf_rn(-s, s, y);
-    return __fmaf_rn(d, __fmul_rn(0.5f, r), s);
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(y));
+    return r;
 }
 
-// sin and cos of 2 pi u for u in [0, 1): x = 4u and r = x - rint(x) are exact,
+// sin and cos of (pi/2) x for x = 4u in [0, 4): r = x - rint(x) is exact,
 // theta = (pi/2) r in [-pi/4, pi/4], sin = r S(r^2), cos = C(r^2), then the
 // quadrant q = rint(x) rotates the pair by q quarter turns.
-__device__ __forceinline__ void sincos2pi(float u, float& s, float& c)
+__device__ __forceinline__ void sincos_quarter(float x, float& s, float& c)
 {
-    const float x = __fmul_rn(4.0f, u);
     const float qf = rintf(x);
     const float r = __fsub_rn(x, qf);
     const int q = (int)qf;
@@ -161,6 +184,12 @@ __device__ __forceinline__ void sincos2pi(float u, float& s, float& c)
     const float co = swap ? st : ct;
     s = (q & 2) ? -so : so;
     c = ((q + 1) & 2) ? -co : co;
+}
+
+// sin and cos of 2 pi u for u in [0, 1) (x = 4u is exact).
+__device__ __forceinline__ void sincos2pi(float u, float& s, float& c)
+{
+    sincos_quarter(__fmul_rn(4.0f, u), s, c);
 }
 
 // Box-Muller pair from two uniforms in (0, 1).
@@ -182,17 +211,36 @@ __device__ __forceinline__ float box_muller_cos(float u1, float u2)
     return __fmul_rn(rho, c);
 }
 
+// The same two transforms from raw 32-bit draws (u = open01_from_u32), with
+// 4u formed directly from the draw.
+__device__ __forceinline__ void box_muller_u32(uint32_t r1, uint32_t r2, float& g1, float& g2)
+{
+    const float rho = sqrt_pos(neg2log(open01_from_u32(r1)));
+    float s, c;
+    sincos_quarter(quarter_turns_from_u32(r2), s, c);
+    g1 = __fmul_rn(rho, c);
+    g2 = __fmul_rn(rho, s);
+}
+
+__device__ __forceinline__ float box_muller_cos_u32(uint32_t r1, uint32_t r2)
+{
+    const float rho = sqrt_pos(neg2log(open01_from_u32(r1)));
+    float s, c;
+    sincos_quarter(quarter_turns_from_u32(r2), s, c);
+    return __fmul_rn(rho, c);
+}
+
 // Three normals of one particle-step from four draws of the generator.
 struct TausDraw {
     uint4 y;
     __device__ __forceinline__ void normals3(float& gx, float& gy, float& gz)
     {
-        const float u1 = open01_from_u32(taus_next(y));
-        const float u2 = open01_from_u32(taus_next(y));
-        const float u3 = open01_from_u32(taus_next(y));
-        const float u4 = open01_from_u32(taus_next(y));
-        box_muller(u1, u2, gx, gy);
-        gz = box_muller_cos(u3, u4);
+        const uint32_t r1 = taus_next(y);
+        const uint32_t r2 = taus_next(y);
+        const uint32_t r3 = taus_next(y);
+        const uint32_t r4 = taus_next(y);
+        box_muller_u32(r1, r2, gx, gy);
+        gz = box_muller_cos_u32(r3, r4);
     }
 };
 
@@ -249,6 +297,37 @@ struct Kahan {
         s = t;
     }
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Time sum of one oscillator's energy E_t = hK |x_t|^2 + hm |v_t|^2, with hK
+// and hm fixed for the oscillator: |x_t|^2 and |v_t|^2 are summed in binary32
+// over blocks of at most kEnergyBlock steps, each block is folded into a Kahan
+// sum, and the energy sum is formed once, in double, from the two sums.
+constexpr int kEnergyBlock = 16;
+
+__device__ __forceinline__ float norm2(float a0, float a1, float a2)
+{
+    return __fmaf_rn(a2, a2, __fmaf_rn(a1, a1, __fmul_rn(a0, a0)));
+}
+
+struct EnergySum {
+    Kahan X, V;
+    float bx = 0.f, bv = 0.f;
+    __device__ __forceinline__ void add(float x0, float x1, float x2, float v0, float v1, float v2)
+    {
+        bx = __fadd_rn(bx, norm2(x0, x1, x2));
+        bv = __fadd_rn(bv, norm2(v0, v1, v2));
+    }
+    __device__ __forceinline__ void flush()
+    {
+        X.add(bx);
+        V.add(bv);
+        bx = bv = 0.f;
+    }
+    __device__ __forceinline__ double value(float hK, float hm) const
+    {
+        return (double)hK * X.value() + (double)hm * V.value();
+    }
 };
 
 // Deterministic block reduction of N doubles per thread (fixed tree order);

@@ -18,10 +18,10 @@ __device__ __forceinline__ void emit_taus(uint4& y, int64_t idx, void* out)
     } else if (MODE == FILL_UNIFORM) {
         ((float*)out)[idx] = u01_from_u32(taus_next(y));
     } else {
-        const float u1 = open01_from_u32(taus_next(y));
-        const float u2 = open01_from_u32(taus_next(y));
+        const uint32_t r1 = taus_next(y);
+        const uint32_t r2 = taus_next(y);
         float2 g;
-        box_muller(u1, u2, g.x, g.y);
+        box_muller_u32(r1, r2, g.x, g.y);
         ((float2*)out)[idx] = g;
     }
 }

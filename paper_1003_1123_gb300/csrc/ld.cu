@@ -4,7 +4,7 @@
 // each, keeps x, v, K_i and the generator state in registers (Ran2's shuffle
 // table in a shared-memory column) for all n_steps; per step it draws four
 // uniforms, forms three Box-Muller normals, applies the Euler-Maruyama update
-// and accumulates the energy.  State goes back to global memory once.
+// and accumulates |x|^2 and |v|^2 for the time-summed energy.  State goes back to global memory once.
 #include "device.cuh"
 #include "internal.cuh"
 
@@ -51,7 +51,8 @@ __global__ void __launch_bounds__(128) ld_pt_kernel(LdArgs a)
 #pragma unroll 4
             for (int j = 0; j < 32; ++j) tab[j * blockDim.x + threadIdx.x] = a.r2[(3 + j) * a.S + i];
         }
-        Kahan e;
+        EnergySum es;
+        float hK = 0.f;
         if (INIT) {
             // draw-step 0 -> x = sqrt(kT/K_i) g, draw-step 1 -> v = sqrt(kT/m) g
             float g0, g1, g2;
@@ -62,14 +63,18 @@ __global__ void __launch_bounds__(128) ld_pt_kernel(LdArgs a)
             v0 = __fmul_rn(c.sv, g0), v1 = __fmul_rn(c.sv, g1), v2 = __fmul_rn(c.sv, g2);
         } else {
             const float ckx = __fmul_rn(c.ckm, Ki);
-            const float hK = 0.5f * Ki;
-            for (int64_t t = 0; t < a.n_steps; ++t) {
-                float g0, g1, g2;
-                if (KIND == GBRNG_TAUS) td.normals3(g0, g1, g2); else rd.normals3(g0, g1, g2);
-                em_component(c.cdt, c.cva, ckx, c.cs, g0, x0, v0);
-                em_component(c.cdt, c.cva, ckx, c.cs, g1, x1, v1);
-                em_component(c.cdt, c.cva, ckx, c.cs, g2, x2, v2);
-                e.add(energy3(hK, c.hm, x0, x1, x2, v0, v1, v2));
+            hK = 0.5f * Ki;
+            for (int64_t t0 = 0; t0 < a.n_steps; t0 += kEnergyBlock) {
+                const int nb = (int)min((int64_t)kEnergyBlock, a.n_steps - t0);
+                for (int k = 0; k < nb; ++k) {
+                    float g0, g1, g2;
+                    if (KIND == GBRNG_TAUS) td.normals3(g0, g1, g2); else rd.normals3(g0, g1, g2);
+                    em_component(c.cdt, c.cva, ckx, c.cs, g0, x0, v0);
+                    em_component(c.cdt, c.cva, ckx, c.cs, g1, x1, v1);
+                    em_component(c.cdt, c.cva, ckx, c.cs, g2, x2, v2);
+                    es.add(x0, x1, x2, v0, v1, v2);
+                }
+                es.flush();
             }
         }
         a.x[3 * i] = x0, a.x[3 * i + 1] = x1, a.x[3 * i + 2] = x2;
@@ -86,7 +91,7 @@ __global__ void __launch_bounds__(128) ld_pt_kernel(LdArgs a)
         acc[0] += (double)x0 * x0 + (double)x1 * x1 + (double)x2 * x2;
         acc[1] += (double)v0 * v0 + (double)v1 * v1 + (double)v2 * v2;
         acc[2] += (double)x0 * v0 + (double)x1 * v1 + (double)x2 * v2;
-        acc[3] += e.value();
+        acc[3] += es.value(hK, c.hm);
     }
     if (a.partials) {
         block_reduce_sum<4>(acc, red);

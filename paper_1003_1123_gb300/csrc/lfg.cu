@@ -230,8 +230,8 @@ __device__ __forceinline__ void walk_blocks(const LfgArgs& a, int64_t q_first, i
 // of the second).
 __device__ __forceinline__ void normals3(uint4 w, float& g0, float& g1, float& g2)
 {
-    box_muller(open01_from_u32(w.x), open01_from_u32(w.y), g0, g1);
-    g2 = box_muller_cos(open01_from_u32(w.z), open01_from_u32(w.w));
+    box_muller_u32(w.x, w.y, g0, g1);
+    g2 = box_muller_cos_u32(w.z, w.w);
 }
 
 // Euler-Maruyama update of one oscillator (x, v in registers), its energy
@@ -278,11 +278,11 @@ __global__ void __launch_bounds__(kLfgThreads, MODE == LFG_LD ? 1 : 2) lfg_kerne
                                 const int i = 4 * lane;
                                 float2 o;
                                 if (i < nval) {
-                                    box_muller(open01_from_u32(w.x), open01_from_u32(w.y), o.x, o.y);
+                                    box_muller_u32(w.x, w.y, o.x, o.y);
                                     __stcs((float2*)((float*)a.out + u0 + i), o);
                                 }
                                 if (i + 2 < nval) {
-                                    box_muller(open01_from_u32(w.z), open01_from_u32(w.w), o.x, o.y);
+                                    box_muller_u32(w.z, w.w, o.x, o.y);
                                     __stcs((float2*)((float*)a.out + u0 + i + 2), o);
                                 }
                             } else {
@@ -350,8 +350,12 @@ __global__ void __launch_bounds__(kLfgThreads, MODE == LFG_LD ? 1 : 2) lfg_kerne
 // When every step of the launch is one all-leap round (4N <= the round width
 // and the launch starts at or above ll), CTA c owns the oscillators
 // [c n_c, c n_c + n_c) for the whole launch and keeps their x and v in shared
-// memory: a step's global traffic is then the ring alone.
-constexpr int kResThreads = 768;
+// memory: a step's global traffic is then the ring alone.  A step's positions
+// for the CTA are one contiguous region; when none of its windows wraps around
+// the ring (all but about one step in R / 4N), each lane addresses the region
+// with one pointer per window and the blocks are walked two at a time, the
+// loads of one in flight while the other is consumed.
+constexpr int kResThreads = 512;
 constexpr int kResWarps = kResThreads / 32;
 
 __global__ void __launch_bounds__(kResThreads, 1) lfg_resident_kernel(LfgArgs a, int64_t n_c)
@@ -361,39 +365,91 @@ __global__ void __launch_bounds__(kResThreads, 1) lfg_resident_kernel(LfgArgs a,
     __shared__ double red[4 * 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t j0 = blockIdx.x * n_c;
-    const int64_t nc = max((int64_t)0, min(a.N, j0 + n_c) - j0);
+    const int nc = (int)max((int64_t)0, min(a.N, j0 + n_c) - j0);
     float* xs = res_sm;
     float* vs = res_sm + 3 * n_c;
-    for (int64_t i = threadIdx.x; i < 3 * nc; i += kResThreads) {
+    for (int i = threadIdx.x; i < 3 * nc; i += kResThreads) {
         xs[i] = __ldcg(a.x + 3 * j0 + i);
         vs[i] = __ldcg(a.v + 3 * j0 + i);
     }
     __syncthreads();
     const bool arrive_here = (int)blockIdx.x != a.stall_cta;
+    const int npos = 4 * nc, nblk = (nc + 31) >> 5;
+    uint32_t* buf = bufs[warp];
     Kahan e;
     double acc[3] = {0, 0, 0};
     for (int64_t t = 0; t < a.n_steps; ++t) {
         const bool last = t == a.n_steps - 1;
-        walk_blocks(a, a.base + 4 * (t * a.N + j0), 4 * nc, warp, kResWarps, bufs[warp],
-                    [&](int64_t b, int nval, uint4 w) {
-                        if (4 * lane >= nval) return;
-                        const int64_t jj = 32 * b + lane;
-                        float g0, g1, g2;
-                        normals3(w, g0, g1, g2);
-                        const float Ki = a.Kper ? __ldg(a.Kper + j0 + jj) : a.c.K;
-                        float* xp = xs + 3 * jj;
-                        float* vp = vs + 3 * jj;
-                        float x0 = xp[0], x1 = xp[1], x2 = xp[2];
-                        float v0 = vp[0], v1 = vp[1], v2 = vp[2];
-                        em_update(a.c, Ki, g0, g1, g2, x0, x1, x2, v0, v1, v2, last, e, acc);
-                        xp[0] = x0, xp[1] = x1, xp[2] = x2;
-                        vp[0] = v0, vp[1] = v1, vp[2] = v2;
-                    });
+        // oscillator jj of this CTA from its four values w
+        auto osc = [&](int jj, uint4 w) {
+            float g0, g1, g2;
+            normals3(w, g0, g1, g2);
+            const float Ki = a.Kper ? __ldg(a.Kper + j0 + jj) : a.c.K;
+            float* xp = xs + 3 * jj;
+            float* vp = vs + 3 * jj;
+            float x0 = xp[0], x1 = xp[1], x2 = xp[2];
+            float v0 = vp[0], v1 = vp[1], v2 = vp[2];
+            em_update(a.c, Ki, g0, g1, g2, x0, x1, x2, v0, v1, v2, last, e, acc);
+            xp[0] = x0, xp[1] = x1, xp[2] = x2;
+            vp[0] = v0, vp[1] = v1, vp[2] = v2;
+        };
+        const int64_t P = a.base + 4 * (t * a.N + j0);
+        const uint32_t P32 = (uint32_t)P;
+        const uint32_t span = 128u * (uint32_t)nblk;   // whole blocks, loads may read past npos
+        const uint32_t sA = (P32 + a.oA) & a.mask, sB = (P32 + a.oB) & a.mask;
+        const uint32_t sC = (P32 + a.oC) & a.mask, sS = P32 & a.mask;
+        const bool fast = span <= a.mask && sA <= a.mask + 1 - span && sB <= a.mask + 1 - span &&
+                          sC <= a.mask + 1 - span && sS <= a.mask + 1 - span;
+        if (fast) {
+            const uint32_t* pA = a.ring + sA + lane;
+            const uint32_t* pB = a.ring + sB + lane;
+            const uint32_t* pC = a.ring + sC + lane;
+            uint32_t* pS = a.ring + sS + lane;
+            auto load = [&](int b, Lags(&g)[4]) {
+                const int o = 128 * b;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    g[k].A = __ldcg(pA + o + 32 * k);
+                    g[k].B = __ldcg(pB + o + 32 * k);
+                    g[k].C = __ldcg(pC + o + 32 * k);
+                }
+            };
+            auto consume = [&](int b, const Lags(&g)[4]) {
+                const int o = 128 * b;
+                const bool whole = o + 128 <= npos;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t val = g[k].value();
+                    if (whole || o + 32 * k + lane < npos) __stcg(pS + o + 32 * k, val);
+                    buf[32 * k + lane] = val;
+                }
+                const uint4 w = block_transpose(buf);
+                const int jj = 32 * b + lane;
+                if (jj < nc) osc(jj, w);
+            };
+            Lags g0[4], g1[4];
+            int b = warp;
+            if (b < nblk) load(b, g0);
+            while (b < nblk) {
+                const int b1 = b + kResWarps;
+                if (b1 < nblk) load(b1, g1);
+                consume(b, g0);
+                if (b1 >= nblk) break;
+                const int b2 = b1 + kResWarps;
+                if (b2 < nblk) load(b2, g0);
+                consume(b1, g1);
+                b = b2;
+            }
+        } else {
+            walk_blocks(a, P, npos, warp, kResWarps, buf, [&](int64_t b, int nval, uint4 w) {
+                if (4 * lane < nval) osc(32 * (int)b + lane, w);
+            });
+        }
         if (!last && !grid_barrier(a, (uint32_t)gridDim.x * (uint32_t)(t + 1), arrive_here))
             return;
     }
     __syncthreads();
-    for (int64_t i = threadIdx.x; i < 3 * nc; i += kResThreads) {
+    for (int i = threadIdx.x; i < 3 * nc; i += kResThreads) {
         __stcg(a.x + 3 * j0 + i, xs[i]);
         __stcg(a.v + 3 * j0 + i, vs[i]);
     }

@@ -64,14 +64,18 @@ __global__ void __launch_bounds__(128) ld_noalloc_kernel(NoallocArgs a)
         }
         const float ckx = __fmul_rn(c.ckm, Ki);
         const float hK = 0.5f * Ki;
-        Kahan e;
-        for (int64_t t = 0; t < a.n_steps; ++t) {
-            float g0, g1, g2;
-            if (KIND == GBRNG_TAUS) td.normals3(g0, g1, g2); else rd.normals3(g0, g1, g2);
-            em_component(c.cdt, c.cva, ckx, c.cs, g0, x0, v0);
-            em_component(c.cdt, c.cva, ckx, c.cs, g1, x1, v1);
-            em_component(c.cdt, c.cva, ckx, c.cs, g2, x2, v2);
-            e.add(energy3(hK, c.hm, x0, x1, x2, v0, v1, v2));
+        EnergySum es;
+        for (int64_t t0 = 0; t0 < a.n_steps; t0 += kEnergyBlock) {
+            const int nb = (int)min((int64_t)kEnergyBlock, a.n_steps - t0);
+            for (int k = 0; k < nb; ++k) {
+                float g0, g1, g2;
+                if (KIND == GBRNG_TAUS) td.normals3(g0, g1, g2); else rd.normals3(g0, g1, g2);
+                em_component(c.cdt, c.cva, ckx, c.cs, g0, x0, v0);
+                em_component(c.cdt, c.cva, ckx, c.cs, g1, x1, v1);
+                em_component(c.cdt, c.cva, ckx, c.cs, g2, x2, v2);
+                es.add(x0, x1, x2, v0, v1, v2);
+            }
+            es.flush();
         }
         a.x[3 * i] = x0, a.x[3 * i + 1] = x1, a.x[3 * i + 2] = x2;
         a.v[3 * i] = v0, a.v[3 * i + 1] = v1, a.v[3 * i + 2] = v2;
@@ -87,7 +91,7 @@ __global__ void __launch_bounds__(128) ld_noalloc_kernel(NoallocArgs a)
         acc[0] += (double)x0 * x0 + (double)x1 * x1 + (double)x2 * x2;
         acc[1] += (double)v0 * v0 + (double)v1 * v1 + (double)v2 * v2;
         acc[2] += (double)x0 * v0 + (double)x1 * v1 + (double)x2 * v2;
-        acc[3] += e.value();
+        acc[3] += es.value(hK, c.hm);
     }
     block_reduce_sum<4>(acc, red);
     if (threadIdx.x == 0)
