@@ -40,7 +40,7 @@ struct Tile {
 };
 
 template <int KIND, int K>
-__global__ void __launch_bounds__(256) batched_kernel(const SysDesc* __restrict__ sys,
+__global__ void __launch_bounds__(256, KIND == GBRNG_TAUS && K == 1 ? 5 : 1) batched_kernel(const SysDesc* __restrict__ sys,
                                                       const Tile* __restrict__ tiles,
                                                       int64_t n_tiles, int64_t n_steps,
                                                       double* __restrict__ partials)

@@ -5,6 +5,8 @@
 // table in a shared-memory column) for all n_steps; per step it draws four
 // uniforms, forms three Box-Muller normals, applies the Euler-Maruyama update
 // and accumulates |x|^2 and |v|^2 for the time-summed energy.  State goes back to global memory once.
+#include <algorithm>
+
 #include "device.cuh"
 #include "internal.cuh"
 
@@ -22,8 +24,10 @@ struct LdArgs {
     double* partials;  // [gridDim.x][4]
 };
 
+// Register budget: 48 per thread for Hybrid Taus (ten 128-thread blocks per
+// SM; measured faster than 64 registers and eight blocks), 56 for Ran2.
 template <int KIND, bool INIT>
-__global__ void __launch_bounds__(128) ld_pt_kernel(LdArgs a)
+__global__ void __launch_bounds__(128, KIND == GBRNG_TAUS ? 10 : 9) ld_pt_kernel(LdArgs a)
 {
     extern __shared__ int32_t tab[];   // Ran2: [32][blockDim.x]
     __shared__ double red[4 * 32];
@@ -101,9 +105,13 @@ __global__ void __launch_bounds__(128) ld_pt_kernel(LdArgs a)
     }
 }
 
-// Grid shape: threads per block T, then the fewest oscillators per thread
-// that fit one resident wave, then as many blocks as needed for that count;
-// every SM receives about the same number of oscillators.
+// Grid shape: threads per block T and one full resident wave (SMs x blocks
+// per SM, fewer only when the system has fewer oscillators than that wave has
+// threads).  Thread g takes oscillators g, g + W, ...; the last, partial round
+// then falls on the lowest blocks, which the block scheduler spreads over all
+// SMs, so every SM carries the same work to within one block's round.  (A grid
+// cut to ceil(n / (oscillators per thread x T)) blocks leaves some SMs a block
+// short and others a block over, about 9% apart at 1e6 oscillators.)
 template <int KIND, bool INIT>
 static int launch_ld(const ld_system* s, int64_t n_steps, bool want_stats, int64_t* blocks_out,
                      cudaStream_t st)
@@ -117,9 +125,7 @@ static int launch_ld(const ld_system* s, int64_t n_steps, bool want_stats, int64
     int occ = 0;
     GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ld_pt_kernel<KIND, INIT>, T, smem));
     if (occ < 1) occ = 1;
-    const int64_t wave = (int64_t)di.sms * occ * T;
-    const int64_t per_thread = (s->n + wave - 1) / wave;
-    int64_t blocks = (s->n + per_thread * T - 1) / (per_thread * T);
+    int64_t blocks = std::min<int64_t>((int64_t)di.sms * occ, (s->n + T - 1) / T);
     if (blocks < 1) blocks = 1;
     if (want_stats) GB_CHECK(ensure_partials(h, blocks));
     LdArgs a;
