@@ -60,6 +60,20 @@ __host__ __device__ __forceinline__ int32_t schrage(int32_t x)
     return y < 0 ? y + M : y;
 }
 
+// The same a*x mod m from the 64-bit product, for m = 2^31 - d: 2^31 = d
+// (mod m), so p = hi 2^31 + lo = hi d + lo (mod m), and hi d + lo < 2^31 + 2^24
+// < 2m needs one conditional subtraction.  Equal to schrage() for every
+// 0 < x < m (checked exhaustively for both moduli); one wide multiply instead
+// of Schrage's quotient and three multiplies.
+template <int32_t A, int32_t M>
+__host__ __device__ __forceinline__ int32_t mulmod_m31(int32_t x)
+{
+    constexpr uint32_t d = 2147483648u - (uint32_t)M;
+    const uint64_t p = (uint64_t)(uint32_t)A * (uint32_t)x;
+    const uint32_t r = (uint32_t)(p >> 31) * d + ((uint32_t)p & 0x7fffffffu);
+    return (int32_t)(r >= (uint32_t)M ? r - (uint32_t)M : r);
+}
+
 // One Ran2 draw; the shuffle table is addressed through `iv(j)` so that it can
 // live in shared memory ([32][threads]) or global memory.
 struct Ran2Regs {
@@ -69,8 +83,8 @@ struct Ran2Regs {
 template <class TableRef>
 __device__ __forceinline__ int32_t ran2_next(Ran2Regs& r, TableRef iv)
 {
-    r.idum = schrage<kR2A1, kR2M1, kR2Q1, kR2R1>(r.idum);
-    r.idum2 = schrage<kR2A2, kR2M2, kR2Q2, kR2R2>(r.idum2);
+    r.idum = mulmod_m31<kR2A1, kR2M1>(r.idum);
+    r.idum2 = mulmod_m31<kR2A2, kR2M2>(r.idum2);
     const int j = (int)((uint32_t)r.iy / (uint32_t)kR2Ndiv);   // previous iy
     int32_t y = iv(j) - r.idum2;
     iv(j) = r.idum;
