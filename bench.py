@@ -134,11 +134,34 @@ class Clocks:
                 "samples": len(rows), "reasons": sorted(reasons)}
 
 
+# ------------------------------------------------------------- replicas
+def rank_seed(rank: int) -> int:
+    """Seed of a rank's replica: independent streams per rank (counter-based
+    seeding, so ranks share no stream)."""
+    return SEED + 1000003 * rank
+
+
+def max_over_ranks(value: float, dist, device: str) -> float:
+    """The slowest rank's time: one all-reduce (MAX) of a scalar, the only
+    collective of a replicas run."""
+    if not dist:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_step: float, ms_per_step: float) -> float:
+    """Units all ranks processed per second (each rank runs the full step)."""
+    return world * units_per_step / (ms_per_step / 1e3)
+
+
 # --------------------------------------------------------------------- GPU
 class Workload:
     def __init__(self, G, torch, rank: int):
         self.G, self.torch = G, torch
-        seed = SEED + 1000003 * rank
+        seed = rank_seed(rank)
         self.systems = {}
         for kind in KINDS:
             r = G.rng_init(kind, seed, N_OSC)
@@ -229,13 +252,9 @@ def run_gpu(args, rank, world, dist):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    elapsed_ms = t_start.elapsed_time(t_end)
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(t_start.elapsed_time(t_end), dist, "cuda")
     ms_per_step = elapsed_ms / args.steps
-    value = world * osc_steps_per_step / (ms_per_step / 1e3)
+    value = whole_job_rate(world, osc_steps_per_step, ms_per_step)
 
     # ---- end to end through host buffers (pinned inputs and outputs)
     e2e = run_e2e(args, wl, parts, G, torch)
