@@ -191,6 +191,19 @@ int ld_init_equilibrium(ld_system* sys, void* stream);
  * K > 0 (or K_per given). */
 int ld_run(ld_system* sys, int64_t n_steps, ld_stats* out_host, void* stream);
 
+/* Paper-form run, the reference form of ld_run (Algorithms 1-3 as printed,
+ * Fig. 2-3, Sec. III.C): one kernel launch per step; every launch loads each
+ * oscillator's generator state (Ran2's shuffle table in global memory), x, v
+ * and its energy sum from global memory, takes one step and stores them back.
+ * Same draws, stream positions and binary32 operations as ld_run, so x, v and
+ * the generator state come out bit for bit equal to ld_run's; the statistics
+ * equal ld_run's up to summation order.  Lagged Fibonacci: a step's 4N
+ * positions must be independent of each other, 4N <= ll - sl while the
+ * generator is below position ll and 4N <= 2 (ll - sl) after (the leap form),
+ * else GBRNG_ELAGS and nothing runs.  Owns 8 bytes of scratch per oscillator
+ * (grown on demand, freed in rng_destroy).  out_host as in ld_run. */
+int ld_run_stepwise(ld_system* sys, int64_t n_steps, ld_stats* out_host, void* stream);
+
 /* Run n_sys independent systems (own handle, parameters and arrays each;
  * per-thread kinds only) as one persistent launch per steps-per-launch chunk,
  * captured once into a CUDA graph.  tune = {threads per block, oscillators

@@ -56,6 +56,8 @@ struct Handle {
     double* partials = nullptr;     // per-block reduction partials
     int64_t partials_cap = 0;
     double* dstats = nullptr;       // 8 doubles of final statistics
+    float2* eacc = nullptr;         // paper-form runs: per-oscillator energy sum (Kahan s, c)
+    int64_t eacc_cap = 0;
 };
 
 // Device attributes used for launch sizing (cached per device).
@@ -91,6 +93,13 @@ int ld_run_pt(const ld_system* s, int64_t n_steps, ld_stats* out, cudaStream_t s
 int lfg_seed(Handle* h, cudaStream_t st);
 int lfg_fill(Handle* h, void* dst, int64_t n, int mode, cudaStream_t st);  // mode 0 u32, 1 uniform, 2 normal
 int lfg_ld(const ld_system* s, int64_t n_steps, int init, ld_stats* out, cudaStream_t st);
+
+// Paper-form runs, one launch per step (stepwise.cu, lfg.cu).
+int ld_run_stepwise_pt(const ld_system* s, int64_t n_steps, ld_stats* out, cudaStream_t st);
+int lfg_ld_stepwise(const ld_system* s, int64_t n_steps, ld_stats* out, cudaStream_t st);
+int ensure_eacc(Handle* h, int64_t n);
+// Final-state sums and the per-oscillator energy sums of a paper-form run.
+int stepwise_stats(Handle* h, const ld_system* s, int64_t n_steps, ld_stats* out, cudaStream_t st);
 
 // Statistics: reduce `blocks` partials (4 doubles each) into h->dstats and
 // copy to the host (synchronising st).

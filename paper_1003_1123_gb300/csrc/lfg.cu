@@ -462,6 +462,44 @@ __global__ void __launch_bounds__(kResThreads, 1) lfg_resident_kernel(LfgArgs a,
     }
 }
 
+// ----------------------------------------------------------- paper form
+// One launch per step (Algorithm 3 with Sec. III.C's one-step-per-launch
+// scheme): thread j computes positions P + 4j .. P + 4j + 3 from the ring,
+// stores them, and takes oscillator j's step with x, v and its energy sum in
+// global memory.  The launch boundary is the only synchronisation, so every
+// position of the step must be dependency-free (checked on the host).
+__global__ void __launch_bounds__(256) lfg_step_kernel(LfgArgs a, int64_t P, float2* eacc)
+{
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= a.N) return;
+    const int64_t q = P + 4 * j;
+    uint32_t w[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) w[r] = load_lags(a, q + r).value();
+#pragma unroll
+    for (int r = 0; r < 4; ++r) a.ring[(uint64_t)(q + r) & a.mask] = w[r];
+    float g0, g1, g2;
+    box_muller_u32(w[0], w[1], g0, g1);
+    g2 = box_muller_cos_u32(w[2], w[3]);
+    const float Ki = a.Kper ? a.Kper[j] : a.c.K;
+    float* xp = a.x + 3 * j;
+    float* vp = a.v + 3 * j;
+    float x0 = xp[0], x1 = xp[1], x2 = xp[2];
+    float v0 = vp[0], v1 = vp[1], v2 = vp[2];
+    const float ckx = __fmul_rn(a.c.ckm, Ki);
+    em_component(a.c.cdt, a.c.cva, ckx, a.c.cs, g0, x0, v0);
+    em_component(a.c.cdt, a.c.cva, ckx, a.c.cs, g1, x1, v1);
+    em_component(a.c.cdt, a.c.cva, ckx, a.c.cs, g2, x2, v2);
+    xp[0] = x0, xp[1] = x1, xp[2] = x2;
+    vp[0] = v0, vp[1] = v1, vp[2] = v2;
+    Kahan e;
+    const float2 ec = eacc[j];
+    e.s = ec.x;
+    e.c = ec.y;
+    e.add(energy3(0.5f * Ki, a.c.hm, x0, x1, x2, v0, v1, v2));
+    eacc[j] = make_float2(e.s, e.c);
+}
+
 // Seeds: ring word for position w - ll (w = 0..ll-1) is the low half of
 // SplitMix64 at counter w; x_{-ll} is forced odd.
 __global__ void lfg_seed_kernel(uint64_t seed, int32_t ll, uint32_t mask, uint32_t* ring)
@@ -668,6 +706,37 @@ int lfg_ld(const ld_system* s, int64_t n_steps, int init, ld_stats* out, cudaStr
     h->pos += a.n_pos;
     if (out) return finish_stats(h, G, n_steps, out, st);
     return GBRNG_OK;
+}
+
+int lfg_ld_stepwise(const ld_system* s, int64_t n_steps, ld_stats* out, cudaStream_t st)
+{
+    Handle* h = s->rng;
+    if (s->n == 0) {
+        if (out) *out = ld_stats{0, 0, 0, 0, n_steps};
+        return GBRNG_OK;
+    }
+    const int64_t D = (int64_t)h->ll - h->sl, R = (int64_t)h->ring_mask + 1;
+    const int64_t four_n = 4 * s->n;
+    if (four_n > std::min(2 * D, R - 2 * (int64_t)h->ll) || (h->pos < h->ll && four_n > D))
+        return fail(GBRNG_ELAGS,
+                    "one launch per step needs 4N = %lld within the lag distance (ll - sl = %lld, "
+                    "twice that from position ll on)",
+                    (long long)four_n, (long long)D);
+    GB_CHECK(ensure_eacc(h, s->n));
+    GB_CUDA(cudaMemsetAsync(h->eacc, 0, sizeof(float2) * s->n, st));
+    LfgArgs a{};
+    set_ring(h, a);
+    a.N = s->n;
+    a.x = s->x;
+    a.v = s->v;
+    a.Kper = s->K_per;
+    a.c = make_coef(s);
+    const unsigned blocks = (unsigned)((s->n + 255) / 256);
+    for (int64_t t = 0; t < n_steps; ++t)
+        lfg_step_kernel<<<blocks, 256, 0, st>>>(a, h->pos + four_n * t, h->eacc);
+    GB_CUDA(cudaGetLastError());
+    h->pos += four_n * n_steps;
+    return stepwise_stats(h, s, n_steps, out, st);
 }
 
 }  // namespace gb

@@ -66,6 +66,20 @@ int ensure_partials(Handle* h, int64_t count)
     return GBRNG_OK;
 }
 
+int ensure_eacc(Handle* h, int64_t n)
+{
+    if (n <= h->eacc_cap) return GBRNG_OK;
+    if (h->eacc) cudaFree(h->eacc);
+    h->eacc = nullptr;
+    h->eacc_cap = 0;
+    if (cudaMalloc(&h->eacc, sizeof(float2) * n) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GBRNG_ENOMEM, "cannot allocate %lld energy sums", (long long)n);
+    }
+    h->eacc_cap = n;
+    return GBRNG_OK;
+}
+
 int ensure_progress(Handle* h, int64_t count)
 {
     if (count <= h->progress_cap) return GBRNG_OK;
@@ -160,6 +174,7 @@ static void free_handle(Handle* h)
     cudaFree(h->dstatus);
     cudaFree(h->partials);
     cudaFree(h->dstats);
+    cudaFree(h->eacc);
     delete static_cast<gbrng_rng*>(h);
 }
 
@@ -531,6 +546,15 @@ int ld_run(ld_system* sys, int64_t n_steps, ld_stats* out, void* stream)
     if (n_steps < 0) return fail(GBRNG_EINVAL, "n_steps must be >= 0");
     if (sys->rng->kind == GBRNG_LAGFIB) return lfg_ld(sys, n_steps, 0, out, (cudaStream_t)stream);
     return ld_run_pt(sys, n_steps, out, (cudaStream_t)stream);
+}
+
+int ld_run_stepwise(ld_system* sys, int64_t n_steps, ld_stats* out, void* stream)
+{
+    GB_CHECK(check_system(sys, true));
+    if (n_steps < 0) return fail(GBRNG_EINVAL, "n_steps must be >= 0");
+    if (sys->rng->kind == GBRNG_LAGFIB)
+        return lfg_ld_stepwise(sys, n_steps, out, (cudaStream_t)stream);
+    return ld_run_stepwise_pt(sys, n_steps, out, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -69,6 +69,8 @@ SIGNATURES = {
     "gbrng_test_stall_chunk": (C.c_int, [C.c_int64]),
     "ld_init_equilibrium": (C.c_int, [C.POINTER(LdSystemC), C.c_void_p]),
     "ld_run": (C.c_int, [C.POINTER(LdSystemC), C.c_int64, C.POINTER(LdStatsC), C.c_void_p]),
+    "ld_run_stepwise": (C.c_int, [C.POINTER(LdSystemC), C.c_int64, C.POINTER(LdStatsC),
+                                  C.c_void_p]),
     "ld_run_batched": (C.c_int, [C.POINTER(LdSystemC), C.c_int, C.c_int64,
                                  C.POINTER(C.c_int), C.POINTER(LdStatsC), C.c_void_p]),
     "ld_backward": (C.c_int, [C.POINTER(LdSystemC), C.c_int64, C.c_int, C.c_void_p,
@@ -282,6 +284,16 @@ def ld_run(system: LdSystem, n_steps: int, stats: bool = True, stream=None):
     cs = system.c_struct()
     st = LdStatsC()
     _check(lib().ld_run(C.byref(cs), n_steps, C.byref(st) if stats else None, _stream(stream)))
+    return _stats(st) if stats else None
+
+
+def ld_run_stepwise(system: LdSystem, n_steps: int, stats: bool = True, stream=None):
+    """The paper form of ld_run: one kernel launch per step, state through
+    global memory (same results as ld_run)."""
+    cs = system.c_struct()
+    st = LdStatsC()
+    _check(lib().ld_run_stepwise(C.byref(cs), n_steps, C.byref(st) if stats else None,
+                                 _stream(stream)))
     return _stats(st) if stats else None
 
 
