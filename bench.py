@@ -44,6 +44,7 @@ L2_FLUSH_BYTES = 256 << 20
 PARAMS = dict(K=1.0, m=1.0, gamma=0.5, kT=1.0, dt=0.01)
 BATCH_SYSTEMS, BATCH_STEPS = 512, 5000
 ADJ_N, ADJ_STEPS, ADJ_CKPT = 10**5, 10**4, 100
+STEPWISE_STEPS = 1000
 WORKLOAD = ("N=1e6 3-D oscillators x 1e4 fused steps per generator (Taus, Ran2, Lagged "
             "Fibonacci row 9) + 2^30 uniform and 2^30 normal fills per generator + 512 uneven "
             "systems (N 1e2..1e5) x 5000 batched steps + adjoint of 1e5 oscillators x 1e4 steps")
@@ -342,9 +343,22 @@ def compare_paths(wl, G, torch, part_ms, steps):
     fwd_ms = a.elapsed_time(b)
     batched_ms = part_ms["batched_taus"] / steps
     adj_ms = part_ms["adjoint_taus"] / steps
-    return {"batched_ms": batched_ms, "per_system_launches_ms": per_system_ms,
-            "batched_speedup": per_system_ms / batched_ms,
-            "adjoint_ms": adj_ms, "forward_ms": fwd_ms, "adjoint_over_forward": adj_ms / fwd_ms}
+    out = {"batched_ms": batched_ms, "per_system_launches_ms": per_system_ms,
+           "batched_speedup": per_system_ms / batched_ms,
+           "adjoint_ms": adj_ms, "forward_ms": fwd_ms, "adjoint_over_forward": adj_ms / fwd_ms}
+    # the paper form (one launch per step, state through global memory) on the
+    # same 1e6-oscillator systems, STEPWISE_STEPS steps, per step vs persistent
+    for kind, sysm in wl.systems.items():
+        a.record()
+        G.ld_run_stepwise(sysm, STEPWISE_STEPS, stats=False)
+        b.record()
+        torch.cuda.synchronize()
+        sw = a.elapsed_time(b) / STEPWISE_STEPS
+        pers = part_ms[f"ld_{kind}"] / steps / LD_STEPS
+        out[f"stepwise_{kind}_us_per_step"] = 1e3 * sw
+        out[f"persistent_{kind}_us_per_step"] = 1e3 * pers
+        out[f"persistent_speedup_{kind}"] = sw / pers
+    return out
 
 
 def run_e2e(args, wl, parts, G, torch):
@@ -590,6 +604,59 @@ def run_case(name: str):
     print(f"case {name} done")
 
 
+def run_sweep():
+    """Time per 1000 steps against N for every generator, persistent and paper
+    form (one launch per step), the state bytes per generator, and the share of
+    a fused step that generating its numbers alone takes (a fill of the same
+    count of normals).  Prints one JSON object; not the bench line."""
+    import torch
+    from paper_1003_1123_gb300 import gbrng as G
+    steps = 1000
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        ev[0].record()
+        fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1])
+
+    rows = []
+    for n in (10**3, 10**4, 10**5, 10**6, 10**7):
+        for kind in KINDS:
+            r = G.rng_init(kind, SEED, n)
+            x = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+            v = torch.zeros_like(x)
+            s = G.LdSystem(r, x, v, **PARAMS)
+            G.ld_init_equilibrium(s)
+            row = {"n": n, "kind": kind, "state_bytes": G.rng_state_bytes(r),
+                   "xv_bytes": 24 * n,
+                   "persistent_ms_per_1000": timed(lambda: G.ld_run(s, steps, stats=False))}
+            try:
+                row["paper_form_ms_per_1000"] = timed(
+                    lambda: G.ld_run_stepwise(s, steps, stats=False))
+            except G.GbrngError as e:
+                row["paper_form_ms_per_1000"] = None
+                row["paper_form"] = str(e)[:120]
+            # the numbers of fill_steps steps (at most 4e8 floats), scaled to 1000 steps
+            fill_steps = max(1, min(steps, 10**8 // n))
+            nums = 4 * n * fill_steps
+            out = torch.empty(nums, dtype=torch.float32, device="cuda")
+            f = G.rng_init(kind, SEED + 1, n)
+            row["fill_normal_ms_same_numbers"] = (timed(lambda: G.rng_fill_normal(f, nums, out=out))
+                                                  * steps / fill_steps)
+            row["rng_share_of_fused"] = (row["fill_normal_ms_same_numbers"]
+                                         / row["persistent_ms_per_1000"])
+            del out, f
+            rows.append(row)
+            del s, x, v, r
+            torch.cuda.empty_cache()
+    return {"sweep": "time per 1000 steps vs N (E2), state bytes (E3), RNG share (E4)",
+            "params": PARAMS, "rows": rows}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -598,9 +665,14 @@ def main():
     ap.add_argument("--impl", default="gbrng", choices=["gbrng", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--case", choices=CASES, help="run one small launch of one part and exit")
+    ap.add_argument("--sweep", action="store_true",
+                    help="print the N sweep (time per 1000 steps, state bytes) and exit")
     args = ap.parse_args()
     if args.case:
         run_case(args.case)
+        return
+    if args.sweep:
+        print(json.dumps(run_sweep()))
         return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
