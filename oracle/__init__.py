@@ -28,8 +28,8 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-TAUS, RAN2, LAGFIB = 0, 1, 2
-KIND_NAMES = {"taus": TAUS, "ran2": RAN2, "lagfib": LAGFIB, "lfg": LAGFIB}
+TAUS, RAN2, LAGFIB, LCG = 0, 1, 2, 3
+KIND_NAMES = {"taus": TAUS, "ran2": RAN2, "lagfib": LAGFIB, "lfg": LAGFIB, "lcg": LCG}
 
 
 def build(force: bool = False) -> str:
@@ -42,6 +42,10 @@ def build(force: bool = False) -> str:
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+class _OuParams(C.Structure):
+    _fields_ = [("k_sp", C.c_double), ("xi", C.c_double), ("kT", C.c_double), ("dt", C.c_double)]
 
 
 class _Gen(C.Structure):
@@ -68,6 +72,9 @@ def lib():
                 "or_taus_seed": (None, [u64, i64, vp]),
                 "or_ran2_seed": (None, [u64, i64, vp]),
                 "or_lfg_seed": (None, [u64, i32, vp]),
+                "or_lcg_seed": (None, [u64, i64, vp]),
+                "or_lcg_next": (u32, [vp]),
+                "or_ou_run_f32": (C.c_int, [G, i64, _OuParams, vp, i64, i64, vp, vp]),
                 "or_seed_streams": (None, [C.c_int, u64, vp, i64, vp]),
                 "or_lfg_table": (C.c_int, [C.c_int, C.POINTER(i32), C.POINTER(i32)]),
                 "or_lfg_default_row": (C.c_int, [i64]),
@@ -137,6 +144,9 @@ class Gen:
         elif self.kind == RAN2:
             self.state = np.zeros((self.n, 35), np.int32)
             L.or_ran2_seed(self.seed, self.n, _ptr(self.state))
+        elif self.kind == LCG:
+            self.state = np.zeros(self.n, np.uint32)
+            L.or_lcg_seed(self.seed, self.n, _ptr(self.state))
         else:
             self.row = lfg_default_row(self.n) if lag_row is None or lag_row < 0 else lag_row
             sl, ll = lfg_table(self.row)
@@ -171,7 +181,11 @@ class Gen:
         idx = np.ascontiguousarray(indices, dtype=np.int64)
         g = cls.__new__(cls)
         g.kind, g.seed, g.n = k, int(seed), len(idx)
-        g.state = np.zeros((len(idx), 4 if k == TAUS else 35), np.uint32 if k == TAUS else np.int32)
+        if k == LCG:
+            g.state = np.zeros(len(idx), np.uint32)
+        else:
+            g.state = np.zeros((len(idx), 4 if k == TAUS else 35),
+                               np.uint32 if k == TAUS else np.int32)
         lib().or_seed_streams(k, g.seed, _ptr(idx), len(idx), _ptr(g.state))
         s = _Gen()
         s.kind, s.n_streams, s.pos = k, len(idx), 0
@@ -377,3 +391,25 @@ def gf2_trinomial_irreducible(ll: int, k: int) -> bool:
     if r < 0:
         raise ValueError("bad trinomial")
     return bool(r)
+
+
+# ------------------------------------------------------- overdamped 1-D run
+def ou_params(k_sp=1.0, xi=1.0, kT=1.0, dt=0.01) -> _OuParams:
+    return _OuParams(float(k_sp), float(xi), float(kT), float(dt))
+
+
+def ou_run_f32(gen: Gen, R: np.ndarray, p: _OuParams, n_steps: int, every: int):
+    """Advance the float32 positions R (in place) by n_steps of Eq. 5; returns
+    (mean, corr) at records r = 0 .. n_steps // every (after r * every steps)."""
+    assert R.dtype == np.float32 and R.flags.c_contiguous
+    n_rec = n_steps // every + 1
+    mean = np.zeros(n_rec, np.float64)
+    corr = np.zeros(n_rec, np.float64)
+    assert lib().or_ou_run_f32(gen.ref, len(R), p, _ptr(R), n_steps, every, _ptr(mean),
+                               _ptr(corr)) == 0
+    return mean, corr
+
+
+def lcg_next(x: np.ndarray) -> int:
+    """One step of the Quick and Dirty LCG on x (uint32[1], in place)."""
+    return lib().or_lcg_next(_ptr(x))

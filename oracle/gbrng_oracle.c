@@ -42,6 +42,14 @@
  *               x' = x + dt v.
  *  R10 ld_init_equilibrium spends two draw-steps: step 0 gives
  *      x = sqrt(kT/K) g, step 1 gives v = sqrt(kT/m) g.
+ *  R12 LCG (Eq. 1, m = 2^32, the "Quick and Dirty" form): x_n = a x_{n-1} + c
+ *      with a = 1664525, c = 1013904223; the output is the new word.  Stream s
+ *      starts from the low 32 bits of SplitMix64 at counter 8*s (R3).
+ *  R13 Overdamped step (Eq. 5): the printed random term g sqrt(2 kT xi dt) is
+ *      the random force times dt; divided by xi (Eq. 4) the displacement is
+ *      g sqrt(2 kT dt / xi) = g sqrt(2 D dt), D = kT/xi.  One normal per
+ *      particle-step: the cosine branch of Box-Muller on two draws (as the
+ *      third normal of R8).
  *
  * FP32 arithmetic order of the Langevin step (both sides implement exactly
  * this; only the transcendental functions of Box-Muller may differ in the last
@@ -141,11 +149,18 @@ void or_seed_streams(int kind, uint64_t seed, const int64_t* idx, int64_t n, voi
                 if (k < 3 && w < lowest[k]) w += lowest[k];
                 y[k] = w;
             }
+        } else if (kind == OR_LCG) {
+            ((uint32_t*)st)[j] = (uint32_t)or_splitmix64(seed, 8u * s);
         } else {
             uint64_t w = or_splitmix64(seed, 8u * s);
             ran2_init_one(1 + (int32_t)(w % (uint64_t)R2_IMM1), (int32_t*)st + 35 * j);
         }
     }
+}
+
+void or_lcg_seed(uint64_t seed, int64_t n, uint32_t* st)
+{
+    for (int64_t s = 0; s < n; ++s) st[s] = (uint32_t)or_splitmix64(seed, 8u * (uint64_t)s);
 }
 
 void or_lfg_seed(uint64_t seed, int32_t ll, uint32_t* ring)
@@ -214,6 +229,13 @@ int32_t or_ran2_next(int32_t* st)
     if (iy < 1) iy += R2_IMM1;
     st[2] = iy;
     return iy;
+}
+
+/* Eq. 1 with m = 2^32 (reading R12): the multiply and add wrap modulo 2^32. */
+uint32_t or_lcg_next(uint32_t* x)
+{
+    *x = 1664525u * *x + 1013904223u;
+    return *x;
 }
 
 /* Recurrence of Algorithm 3 for the next position p = pos. */
@@ -286,6 +308,7 @@ static uint32_t draw_u32(or_gen* g, int64_t j)
 {
     if (g->kind == OR_TAUS) return or_taus_next((uint32_t*)g->state + 4 * j);
     if (g->kind == OR_RAN2) return (uint32_t)or_ran2_next((int32_t*)g->state + 35 * j);
+    if (g->kind == OR_LCG) return or_lcg_next((uint32_t*)g->state + j);
     return or_lfg_next(g);
 }
 
@@ -594,7 +617,8 @@ int or_ld_adjoint_f64(or_gen* g, int64_t n, const double* Kper, or_params p, dou
                       double* v, int64_t n_steps, double* loss_per_osc, double* dK,
                       double* dgamma, double* dkT)
 {
-    if (g->kind == OR_LAGFIB || n < 0 || n_steps <= 0 || !params_ok(p) || p.gamma <= 0 ||
+    if (g->kind == OR_LAGFIB || g->kind == OR_LCG || n < 0 || n_steps <= 0 || !params_ok(p) ||
+        p.gamma <= 0 ||
         p.kT <= 0)
         return -1;
     const int64_t S = n_steps;
@@ -662,6 +686,46 @@ int or_ld_adjoint_f64(or_gen* g, int64_t n, const double* Kper, or_params p, dou
 /* ------------------------------------------------------------------------
  * Pins: brute-force periods and GF(2) irreducibility
  * ---------------------------------------------------------------------- */
+
+/* ------------------------------------------------------------------------
+ * Overdamped 1-D Langevin dynamics (Eq. 4-5, reading R13)
+ * ---------------------------------------------------------------------- */
+
+int or_ou_run_f32(or_gen* g, int64_t n, or_ou_params p, float* R, int64_t n_steps,
+                  int64_t every, double* mean, double* corr)
+{
+    if (n < 1 || n_steps < 0 || every < 1 || !(p.k_sp > 0) || !(p.xi > 0) || !(p.kT >= 0) ||
+        !(p.dt > 0))
+        return -1;
+    const float c1 = (float)(p.k_sp * p.dt / p.xi);
+    const float cs = (float)sqrt(2.0 * p.kT * p.dt / p.xi);
+    float* R0 = (float*)malloc(sizeof(float) * (size_t)n);
+    if (!R0) return -1;
+    memcpy(R0, R, sizeof(float) * (size_t)n);
+    int64_t rec = 0;
+    for (int64_t t = 0; t <= n_steps; ++t) {
+        if (t % every == 0) {
+            double sm = 0.0, sc = 0.0;
+            for (int64_t i = 0; i < n; ++i) {
+                sm += (double)R[i];
+                sc += (double)R[i] * (double)R0[i];
+            }
+            mean[rec] = sm / (double)n;
+            corr[rec] = sc / (double)n;
+            ++rec;
+        }
+        if (t == n_steps) break;
+        /* step-major, so the shared sequence is consumed in position order */
+        for (int64_t i = 0; i < n; ++i) {
+            float u1 = draw_bm_f32(g, i), u2 = draw_bm_f32(g, i);
+            float gc, gs;
+            or_box_muller_f32(u1, u2, &gc, &gs);
+            R[i] = fmaf(cs, gc, fmaf(-c1, R[i], R[i]));
+        }
+    }
+    free(R0);
+    return 0;
+}
 
 uint64_t or_taus_component_period(int which, uint32_t seed)
 {

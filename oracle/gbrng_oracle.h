@@ -21,7 +21,7 @@
 extern "C" {
 #endif
 
-enum { OR_TAUS = 0, OR_RAN2 = 1, OR_LAGFIB = 2 };
+enum { OR_TAUS = 0, OR_RAN2 = 1, OR_LAGFIB = 2, OR_LCG = 3 };
 
 /* One generator bundle.  Per-thread kinds hold n_streams independent
  * streams; the Lagged Fibonacci kind holds one shared sequence (ring of ll
@@ -33,7 +33,8 @@ typedef struct {
     int64_t pos;         /* Lagged Fibonacci: next sequence position p >= 0   */
     void*   state;       /* Taus: uint32[n][4]  (y1,y2,y3,y4)
                             Ran2: int32[n][35]  (idum, idum2, iy, iv[32])
-                            Lagged Fibonacci: uint32[ll] ring              */
+                            Lagged Fibonacci: uint32[ll] ring
+                            LCG: uint32[n]                                 */
 } or_gen;
 
 /* ---- seeding (Sec. III.B; counter-based reading) ---------------------- */
@@ -41,6 +42,7 @@ uint64_t or_splitmix64(uint64_t seed, uint64_t idx);
 void     or_taus_seed(uint64_t seed, int64_t n, uint32_t* st);
 void     or_ran2_seed(uint64_t seed, int64_t n, int32_t* st);
 void     or_lfg_seed(uint64_t seed, int32_t ll, uint32_t* ring);
+void     or_lcg_seed(uint64_t seed, int64_t n, uint32_t* st);
 void     or_seed_streams(int kind, uint64_t seed, const int64_t* idx, int64_t n, void* st);
 int      or_lfg_table(int row, int32_t* sl, int32_t* ll);   /* Table I */
 int      or_lfg_default_row(int64_t n_threads);
@@ -51,6 +53,7 @@ uint32_t or_taus_component(uint32_t y, int which);  /* one Tausworthe step */
 int32_t  or_ran2_schrage(int32_t x, int which);     /* a*x mod m, Schrage */
 int32_t  or_ran2_next(int32_t* st);                 /* Algorithm 2 */
 uint32_t or_lfg_next(or_gen* g);                    /* Algorithm 3 */
+uint32_t or_lcg_next(uint32_t* x);                  /* Eq. 1, m = 2^32 */
 
 /* ---- conversions ------------------------------------------------------ */
 float  or_u01_f32(uint32_t raw);          /* fl(raw) * 2^-32, in [0,1]       */
@@ -85,6 +88,17 @@ int or_ld_adjoint_f64(or_gen* g, int64_t n, const double* Kper, or_params p,
                       double* x, double* v, int64_t n_steps,
                       double* loss_per_osc, double* dK, double* dgamma,
                       double* dkT);
+
+/* ---- overdamped 1-D Langevin (Eq. 4-5) ---------------------------------- */
+typedef struct { double k_sp, xi, kT, dt; } or_ou_params;
+/* R' = fma(cs, g, fma(-c1, R, R)) with c1 = fl(k_sp dt / xi) and
+ * cs = fl(sqrt(2 kT dt / xi)) (double expressions rounded once), g the cosine
+ * branch of Box-Muller on two draws per particle-step (shared sequence:
+ * particle i at step t uses positions p0 + 2(i + n t) + r).  Records
+ * r = 0 .. n_steps/every after r*every steps: mean[r] = (1/n) sum_i R_i and
+ * corr[r] = (1/n) sum_i R_i R_i(0), R(0) the positions on entry. */
+int or_ou_run_f32(or_gen* g, int64_t n, or_ou_params p, float* R, int64_t n_steps,
+                  int64_t every, double* mean, double* corr);
 
 /* ---- pins ------------------------------------------------------------- */
 uint64_t or_taus_component_period(int which, uint32_t seed);
