@@ -37,7 +37,7 @@
 extern "C" {
 #endif
 
-typedef enum { GBRNG_TAUS = 0, GBRNG_RAN2 = 1, GBRNG_LAGFIB = 2 } gbrng_kind;
+typedef enum { GBRNG_TAUS = 0, GBRNG_RAN2 = 1, GBRNG_LAGFIB = 2, GBRNG_LCG = 3 } gbrng_kind;
 
 typedef enum {
     GBRNG_OK = 0,
@@ -61,9 +61,15 @@ typedef struct gbrng_rng* gbrng_t;   /* opaque generator handle */
  * Lagged Fibonacci (Algorithm 3): one shared sequence; n_streams is the
  *   number N of threads (oscillators) per step, which selects the Table I row:
  *   the smallest row with sl > 4N and ll - sl > 4N, else the last row.
+ * Quick and Dirty LCG (Eq. 1, m = 2^32: x <- 1664525 x + 1013904223, output
+ *   the new word): n_streams independent streams, one uint32 each.  The
+ *   paper's speed benchmark and statistical negative control; fills, ld_run,
+ *   ld_run_stepwise and ou_run accept it, ld_run_batched, ld_backward and
+ *   ld_run_noalloc return GBRNG_EINVAL.
  * Seeding (Sec. III.B asks for an independent source): word k of stream s is
  * the low 32 bits of SplitMix64 at counter 8s+k; Taus words 1-3 below 2, 8,
- * 16 are raised by 2, 8, 16; Ran2 idum = 1 + (word mod (m1-1)); Lagged
+ * 16 are raised by 2, 8, 16; Ran2 idum = 1 + (word mod (m1-1)); the LCG word
+ * is word 0 of its stream as it stands; Lagged
  * Fibonacci seed w (x_{w-ll}) uses counter w, and x_{-ll} is forced odd.
  * Seeding runs on the GPU.  n_streams >= 1.  *out receives the handle. */
 int rng_init(gbrng_t* out, int kind, uint64_t seed, int64_t n_streams, void* stream);
@@ -190,6 +196,36 @@ int ld_init_equilibrium(ld_system* sys, void* stream);
  * Requirements: n >= 0, n_steps >= 0, m > 0, dt > 0, gamma >= 0, kT >= 0,
  * K > 0 (or K_per given). */
 int ld_run(ld_system* sys, int64_t n_steps, ld_stats* out_host, void* stream);
+
+/* ----------------------------------------------- overdamped 1-D Langevin */
+
+/* n independent 1-D particles in the harmonic potential V = k_sp R^2 / 2
+ * under overdamped Langevin dynamics (Sec. IV, Eq. 4-5): caller-owned device
+ * array R of n binary32 positions. */
+typedef struct {
+    int64_t n;
+    float* R;
+    double k_sp, xi, kT, dt;
+    gbrng_t rng;          /* per-thread kinds need n_streams >= n */
+} ou_system;
+
+/* Advance by n_steps of Eq. 5, R' = R - (k_sp dt / xi) R + g sqrt(2 kT dt / xi)
+ * (the printed random term g sqrt(2 kT xi dt) is the random force times dt;
+ * Eq. 4 divides it by xi), in binary32 as R' = fma(cs, g, fma(-c1, R, R)) with
+ * c1 = fl(k_sp dt / xi) and cs = fl(sqrt(2 kT dt / xi)) (double expressions
+ * rounded once).  One normal per particle-step: the cosine branch of
+ * Box-Muller on two draws (per-thread kinds: stream i; Lagged Fibonacci:
+ * positions p0 + 2(i + n t) + r, r = 0, 1).  Records r = 0 .. n_steps/every
+ * after r*every steps: mean_host[r] = (1/n) sum_i R_i and corr_host[r] =
+ * (1/n) sum_i R_i R_i(0), R(0) the positions on entry (the paper's <R(t)> and
+ * <R(t)R(0)>); both are host arrays of n_steps/every + 1 doubles, or both NULL
+ * (no records).  Lagged Fibonacci: every step is one round of 2n positions,
+ * 2n <= ll - sl below position ll and <= 2(ll - sl) after, else GBRNG_ELAGS and
+ * nothing runs.  Requirements: n >= 1, n_steps >= 0, every >= 1, k_sp > 0,
+ * xi > 0, kT >= 0, dt > 0.  Synchronises the stream when records are
+ * requested; scratch (16 bytes per record per 256 particles) is the handle's. */
+int ou_run(ou_system* sys, int64_t n_steps, int64_t every, double* mean_host, double* corr_host,
+           void* stream);
 
 /* Paper-form run, the reference form of ld_run (Algorithms 1-3 as printed,
  * Fig. 2-3, Sec. III.C): one kernel launch per step; every launch loads each

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgbrng.so")
 
 SOURCES = ["runtime.cu", "fill.cu", "ld.cu", "lfg.cu", "batched.cu", "adjoint.cu", "noalloc.cu",
-           "stepwise.cu"]
+           "stepwise.cu", "ou.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                 "-I", CSRC]

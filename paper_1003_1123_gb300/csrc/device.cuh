@@ -7,6 +7,7 @@
 #include <cstdint>
 
 #include "bm_coeffs.cuh"
+#include "gbrng.h"
 
 namespace gb {
 
@@ -39,6 +40,18 @@ __device__ __forceinline__ uint32_t taus_next(uint4& s)
     s.w = 1664525u * s.w + 1013904223u;
     return s.x ^ s.y ^ s.z ^ s.w;
 }
+
+// ------------------------------------------------------ Quick and Dirty LCG
+// Eq. 1 with m = 2^32: the multiply and add wrap; the output is the new word.
+__device__ __forceinline__ uint32_t lcg_next(uint32_t& x)
+{
+    x = 1664525u * x + 1013904223u;
+    return x;
+}
+
+// The per-thread 32-bit generators behind one name for the fill kernels.
+__device__ __forceinline__ uint32_t next_word(uint4& y) { return taus_next(y); }
+__device__ __forceinline__ uint32_t next_word(uint32_t& x) { return lcg_next(x); }
 
 // -------------------------------------------------------------------- Ran2
 // L'Ecuyer's pair (m1, a1) = (2147483563, 40014), (m2, a2) = (2147483399,
@@ -258,6 +271,19 @@ struct TausDraw {
     }
 };
 
+struct LcgDraw {
+    uint32_t x;
+    __device__ __forceinline__ void normals3(float& gx, float& gy, float& gz)
+    {
+        const uint32_t r1 = lcg_next(x);
+        const uint32_t r2 = lcg_next(x);
+        const uint32_t r3 = lcg_next(x);
+        const uint32_t r4 = lcg_next(x);
+        box_muller_u32(r1, r2, gx, gy);
+        gz = box_muller_cos_u32(r3, r4);
+    }
+};
+
 struct Ran2Draw {
     Ran2Regs r;
     int32_t* tab;
@@ -278,6 +304,19 @@ struct Ran2Draw {
         gz = box_muller_cos(u3, u4);
     }
 };
+
+// Three normals of one particle-step from the per-thread generator KIND.
+template <int KIND>
+__device__ __forceinline__ void draw3(TausDraw& td, LcgDraw& lc, Ran2Draw& rd, float& g0, float& g1,
+                                      float& g2)
+{
+    if (KIND == GBRNG_TAUS)
+        td.normals3(g0, g1, g2);
+    else if (KIND == GBRNG_LCG)
+        lc.normals3(g0, g1, g2);
+    else
+        rd.normals3(g0, g1, g2);
+}
 
 // ------------------------------------------------------------------ LD step
 // v' = fma(cva, v, fma(-ckx, x, cs * g)),  x' = fma(cdt, v, x).

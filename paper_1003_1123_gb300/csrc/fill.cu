@@ -10,16 +10,16 @@ namespace gb {
 
 enum { FILL_U32 = 0, FILL_UNIFORM = 1, FILL_NORMAL = 2 };
 
-template <int MODE>
-__device__ __forceinline__ void emit_taus(uint4& y, int64_t idx, void* out)
+template <int MODE, class State>
+__device__ __forceinline__ void emit_word(State& y, int64_t idx, void* out)
 {
     if (MODE == FILL_U32) {
-        ((uint32_t*)out)[idx] = taus_next(y);
+        ((uint32_t*)out)[idx] = next_word(y);
     } else if (MODE == FILL_UNIFORM) {
-        ((float*)out)[idx] = u01_from_u32(taus_next(y));
+        ((float*)out)[idx] = u01_from_u32(next_word(y));
     } else {
-        const uint32_t r1 = taus_next(y);
-        const uint32_t r2 = taus_next(y);
+        const uint32_t r1 = next_word(y);
+        const uint32_t r2 = next_word(y);
         float2 g;
         box_muller_u32(r1, r2, g.x, g.y);
         ((float2*)out)[idx] = g;
@@ -27,23 +27,24 @@ __device__ __forceinline__ void emit_taus(uint4& y, int64_t idx, void* out)
 }
 
 // n_items = numbers (u32, uniform) or pairs (normal).
-template <int MODE>
-__global__ void __launch_bounds__(256) taus_fill_kernel(uint4* __restrict__ st, int64_t S,
+// Hybrid Taus (uint4 state) and the LCG (uint32 state): one word chain per stream.
+template <int MODE, class State>
+__global__ void __launch_bounds__(256) word_fill_kernel(State* __restrict__ st, int64_t S,
                                                         int64_t n_items, void* __restrict__ out)
 {
     const int64_t active = S < n_items ? S : n_items;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < active; s += stride) {
-        uint4 y = st[s];
+        State y = st[s];
         int64_t idx = s;
         // four draws in flight per iteration: independent stores, one state chain
         for (; idx + 3 * S < n_items; idx += 4 * S) {
-            emit_taus<MODE>(y, idx, out);
-            emit_taus<MODE>(y, idx + S, out);
-            emit_taus<MODE>(y, idx + 2 * S, out);
-            emit_taus<MODE>(y, idx + 3 * S, out);
+            emit_word<MODE>(y, idx, out);
+            emit_word<MODE>(y, idx + S, out);
+            emit_word<MODE>(y, idx + 2 * S, out);
+            emit_word<MODE>(y, idx + 3 * S, out);
         }
-        for (; idx < n_items; idx += S) emit_taus<MODE>(y, idx, out);
+        for (; idx < n_items; idx += S) emit_word<MODE>(y, idx, out);
         st[s] = y;
     }
 }
@@ -88,14 +89,23 @@ static int fill_pt(Handle* h, void* dst, int64_t n_items, cudaStream_t st)
     DevInfo di;
     GB_CHECK(dev_info(h->device, &di));
     const int64_t active = h->n < n_items ? h->n : n_items;
-    if (h->kind == GBRNG_TAUS) {
+    if (h->kind == GBRNG_TAUS || h->kind == GBRNG_LCG) {
         const int T = 256;
         int occ = 0;
-        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, taus_fill_kernel<MODE>, T, 0));
+        if (h->kind == GBRNG_TAUS)
+            GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &occ, word_fill_kernel<MODE, uint4>, T, 0));
+        else
+            GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &occ, word_fill_kernel<MODE, uint32_t>, T, 0));
         int64_t blocks = (active + T - 1) / T;
         const int64_t cap = (int64_t)di.sms * (occ > 0 ? occ : 1);
         if (blocks > cap) blocks = cap;
-        taus_fill_kernel<MODE><<<(unsigned)blocks, T, 0, st>>>(h->taus, h->n, n_items, dst);
+        if (h->kind == GBRNG_TAUS)
+            word_fill_kernel<MODE, uint4><<<(unsigned)blocks, T, 0, st>>>(h->taus, h->n, n_items, dst);
+        else
+            word_fill_kernel<MODE, uint32_t><<<(unsigned)blocks, T, 0, st>>>(h->lcg, h->n, n_items,
+                                                                            dst);
     } else {
         const int T = 128;
         const size_t smem = sizeof(int32_t) * 32 * T;

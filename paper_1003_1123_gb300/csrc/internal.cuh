@@ -40,6 +40,7 @@ struct Handle {
 
     uint4* taus = nullptr;     // [n] (y1, y2, y3, y4)
     int32_t* r2 = nullptr;     // [35][n]: idum, idum2, iy, iv[0..31]
+    uint32_t* lcg = nullptr;   // [n] Quick and Dirty LCG words
 
     // Lagged Fibonacci: the sequence value at position p lives in
     // ring[p & ring_mask]; ring size R = ring_mask + 1 >= 2 ll + 2 (ll - sl).
@@ -100,6 +101,19 @@ int lfg_ld_stepwise(const ld_system* s, int64_t n_steps, ld_stats* out, cudaStre
 int ensure_eacc(Handle* h, int64_t n);
 // Final-state sums and the per-oscillator energy sums of a paper-form run.
 int stepwise_stats(Handle* h, const ld_system* s, int64_t n_steps, ld_stats* out, cudaStream_t st);
+
+// Overdamped 1-D runs (ou.cu, lfg.cu).  Records land in
+// partials[(rec * blocks + block) * 2 + {0, 1}] (sums of R and R R0).
+struct OuCoef {
+    float c1, cs;
+};
+OuCoef make_ou_coef(const ou_system* s);
+int ou_run_pt(const ou_system* s, int64_t n_steps, int64_t every, double* mean, double* corr,
+              cudaStream_t st);
+int lfg_ou(const ou_system* s, int64_t n_steps, int64_t every, double* mean, double* corr,
+           cudaStream_t st);
+int ou_finish(Handle* h, int64_t n, int64_t n_rec, int64_t blocks, double* mean, double* corr,
+              cudaStream_t st);
 
 // Statistics: reduce `blocks` partials (4 doubles each) into h->dstats and
 // copy to the host (synchronising st).

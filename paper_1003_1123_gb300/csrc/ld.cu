@@ -20,14 +20,16 @@ struct LdArgs {
     LdCoef c;
     uint4* taus;       // Taus state [streams]
     int32_t* r2;       // Ran2 state [35][streams]
+    uint32_t* lcg;     // LCG state [streams]
     int64_t S;         // streams of the generator (row stride of r2)
     double* partials;  // [gridDim.x][4]
 };
 
-// Register budget: 48 per thread for Hybrid Taus (ten 128-thread blocks per
-// SM; measured faster than 64 registers and eight blocks), 56 for Ran2.
+// Register budget: 48 per thread for Hybrid Taus and the LCG (ten 128-thread
+// blocks per SM; measured faster than 64 registers and eight blocks), 56 for
+// Ran2.
 template <int KIND, bool INIT>
-__global__ void __launch_bounds__(128, KIND == GBRNG_TAUS ? 10 : 9) ld_pt_kernel(LdArgs a)
+__global__ void __launch_bounds__(128, KIND == GBRNG_RAN2 ? 9 : 10) ld_pt_kernel(LdArgs a)
 {
     extern __shared__ int32_t tab[];   // Ran2: [32][blockDim.x]
     __shared__ double red[4 * 32];
@@ -42,9 +44,12 @@ __global__ void __launch_bounds__(128, KIND == GBRNG_TAUS ? 10 : 9) ld_pt_kernel
             v0 = a.v[3 * i], v1 = a.v[3 * i + 1], v2 = a.v[3 * i + 2];
         }
         TausDraw td;
+        LcgDraw lc;
         Ran2Draw rd;
         if (KIND == GBRNG_TAUS) {
             td.y = a.taus[i];
+        } else if (KIND == GBRNG_LCG) {
+            lc.x = a.lcg[i];
         } else {
             rd.tab = tab;
             rd.T = blockDim.x;
@@ -60,10 +65,10 @@ __global__ void __launch_bounds__(128, KIND == GBRNG_TAUS ? 10 : 9) ld_pt_kernel
         if (INIT) {
             // draw-step 0 -> x = sqrt(kT/K_i) g, draw-step 1 -> v = sqrt(kT/m) g
             float g0, g1, g2;
-            if (KIND == GBRNG_TAUS) td.normals3(g0, g1, g2); else rd.normals3(g0, g1, g2);
+            draw3<KIND>(td, lc, rd, g0, g1, g2);
             const float sx = __fsqrt_rn(__fdiv_rn(c.kT, Ki));
             x0 = __fmul_rn(sx, g0), x1 = __fmul_rn(sx, g1), x2 = __fmul_rn(sx, g2);
-            if (KIND == GBRNG_TAUS) td.normals3(g0, g1, g2); else rd.normals3(g0, g1, g2);
+            draw3<KIND>(td, lc, rd, g0, g1, g2);
             v0 = __fmul_rn(c.sv, g0), v1 = __fmul_rn(c.sv, g1), v2 = __fmul_rn(c.sv, g2);
         } else {
             const float ckx = __fmul_rn(c.ckm, Ki);
@@ -72,7 +77,7 @@ __global__ void __launch_bounds__(128, KIND == GBRNG_TAUS ? 10 : 9) ld_pt_kernel
                 const int nb = (int)min((int64_t)kEnergyBlock, a.n_steps - t0);
                 for (int k = 0; k < nb; ++k) {
                     float g0, g1, g2;
-                    if (KIND == GBRNG_TAUS) td.normals3(g0, g1, g2); else rd.normals3(g0, g1, g2);
+                    draw3<KIND>(td, lc, rd, g0, g1, g2);
                     em_component(c.cdt, c.cva, ckx, c.cs, g0, x0, v0);
                     em_component(c.cdt, c.cva, ckx, c.cs, g1, x1, v1);
                     em_component(c.cdt, c.cva, ckx, c.cs, g2, x2, v2);
@@ -85,6 +90,8 @@ __global__ void __launch_bounds__(128, KIND == GBRNG_TAUS ? 10 : 9) ld_pt_kernel
         a.v[3 * i] = v0, a.v[3 * i + 1] = v1, a.v[3 * i + 2] = v2;
         if (KIND == GBRNG_TAUS) {
             a.taus[i] = td.y;
+        } else if (KIND == GBRNG_LCG) {
+            a.lcg[i] = lc.x;
         } else {
             a.r2[i] = rd.r.idum;
             a.r2[a.S + i] = rd.r.idum2;
@@ -137,6 +144,7 @@ static int launch_ld(const ld_system* s, int64_t n_steps, bool want_stats, int64
     a.c = make_coef(s);
     a.taus = h->taus;
     a.r2 = h->r2;
+    a.lcg = h->lcg;
     a.S = h->n;
     a.partials = want_stats ? h->partials : nullptr;
     ld_pt_kernel<KIND, INIT><<<(unsigned)blocks, T, smem, st>>>(a);
@@ -149,6 +157,7 @@ int ld_init_pt(const ld_system* s, cudaStream_t st)
 {
     int64_t blocks = 0;
     if (s->rng->kind == GBRNG_TAUS) return launch_ld<GBRNG_TAUS, true>(s, 0, false, &blocks, st);
+    if (s->rng->kind == GBRNG_LCG) return launch_ld<GBRNG_LCG, true>(s, 0, false, &blocks, st);
     return launch_ld<GBRNG_RAN2, true>(s, 0, false, &blocks, st);
 }
 
@@ -162,6 +171,8 @@ int ld_run_pt(const ld_system* s, int64_t n_steps, ld_stats* out, cudaStream_t s
     const bool want = out != nullptr;
     if (s->rng->kind == GBRNG_TAUS)
         GB_CHECK((launch_ld<GBRNG_TAUS, false>(s, n_steps, want, &blocks, st)));
+    else if (s->rng->kind == GBRNG_LCG)
+        GB_CHECK((launch_ld<GBRNG_LCG, false>(s, n_steps, want, &blocks, st)));
     else
         GB_CHECK((launch_ld<GBRNG_RAN2, false>(s, n_steps, want, &blocks, st)));
     return finish_stats(s->rng, blocks, n_steps, out, st);

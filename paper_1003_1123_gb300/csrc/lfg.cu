@@ -500,6 +500,51 @@ __global__ void __launch_bounds__(256) lfg_step_kernel(LfgArgs a, int64_t P, flo
     eacc[j] = make_float2(e.s, e.c);
 }
 
+// ------------------------------------------------------ overdamped 1-D run
+// Each step is one round of 2N positions (particle j uses P + 2j, P + 2j + 1),
+// computed by the cooperative grid and closed by the grid barrier; R lives in
+// global memory, R(0) in the handle's scratch.  Records before a step sum each
+// block's particles (R and R R(0) are read by the thread that wrote them).
+__global__ void __launch_bounds__(256) lfg_ou_kernel(LfgArgs a, OuCoef c, float* R, const float* R0,
+                                                     int64_t every, double* partials)
+{
+    __shared__ double red[2 * 32];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool arrive_here = (int)blockIdx.x != a.stall_cta;
+    int64_t rec = 0, next_rec = 0;
+    for (int64_t t = 0;; ++t) {
+        if (partials && t == next_rec) {
+            next_rec += every;
+            double v[2] = {0, 0};
+            for (int64_t j = gt; j < a.N; j += stride) {
+                v[0] += (double)R[j];
+                v[1] += (double)R[j] * (double)R0[j];
+            }
+            block_reduce_sum<2>(v, red);
+            if (threadIdx.x == 0) {
+                double* o = partials + 2 * (rec * gridDim.x + blockIdx.x);
+                o[0] = v[0];
+                o[1] = v[1];
+            }
+            ++rec;
+        }
+        if (t == a.n_steps) break;
+        const int64_t P = a.base + 2 * a.N * t;
+        for (int64_t j = gt; j < a.N; j += stride) {
+            const int64_t q = P + 2 * j;
+            const uint32_t w0 = load_lags(a, q).value(), w1 = load_lags(a, q + 1).value();
+            __stcg(a.ring + ((uint64_t)q & a.mask), w0);
+            __stcg(a.ring + ((uint64_t)(q + 1) & a.mask), w1);
+            const float g = box_muller_cos_u32(w0, w1);
+            R[j] = __fmaf_rn(c.cs, g, __fmaf_rn(-c.c1, R[j], R[j]));
+        }
+        if (t + 1 < a.n_steps &&
+            !grid_barrier(a, (uint32_t)gridDim.x * (uint32_t)(t + 1), arrive_here))
+            return;
+    }
+}
+
 // Seeds: ring word for position w - ll (w = 0..ll-1) is the low half of
 // SplitMix64 at counter w; x_{-ll} is forced odd.
 __global__ void lfg_seed_kernel(uint64_t seed, int32_t ll, uint32_t mask, uint32_t* ring)
@@ -737,6 +782,52 @@ int lfg_ld_stepwise(const ld_system* s, int64_t n_steps, ld_stats* out, cudaStre
     GB_CUDA(cudaGetLastError());
     h->pos += four_n * n_steps;
     return stepwise_stats(h, s, n_steps, out, st);
+}
+
+int lfg_ou(const ou_system* s, int64_t n_steps, int64_t every, double* mean, double* corr,
+           cudaStream_t st)
+{
+    Handle* h = s->rng;
+    const int64_t D = (int64_t)h->ll - h->sl, Rsz = (int64_t)h->ring_mask + 1;
+    const int64_t two_n = 2 * s->n;
+    if (two_n > std::min(2 * D, Rsz - 2 * (int64_t)h->ll) || (h->pos < h->ll && two_n > D))
+        return fail(GBRNG_ELAGS,
+                    "one round per step needs 2N = %lld within the lag distance (ll - sl = %lld, "
+                    "twice that from position ll on)",
+                    (long long)two_n, (long long)D);
+    DevInfo di;
+    GB_CHECK(dev_info(h->device, &di));
+    int occ = 0;
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lfg_ou_kernel, 256, 0));
+    if (occ < 1) return fail(GBRNG_EINVAL, "overdamped kernel does not fit on an SM");
+    const int64_t G = std::min<int64_t>((int64_t)di.sms * occ, (s->n + 255) / 256);
+    const bool rec = mean != nullptr;
+    const int64_t n_rec = n_steps / every + 1;
+    if (rec) {
+        if (n_rec > 0x7fffffff || (double)n_rec * G * 16.0 > 4.0 * (1 << 30))
+            return fail(GBRNG_EINVAL, "%lld records x %lld blocks exceed the record scratch",
+                        (long long)n_rec, (long long)G);
+        GB_CHECK(ensure_partials(h, (2 * n_rec * G + 2 * n_rec + 3) / 4));
+    }
+    GB_CHECK(ensure_eacc(h, s->n));
+    float* R0 = reinterpret_cast<float*>(h->eacc);
+    GB_CUDA(cudaMemcpyAsync(R0, s->R, sizeof(float) * s->n, cudaMemcpyDeviceToDevice, st));
+    LfgArgs a{};
+    set_ring(h, a);
+    a.N = s->n;
+    a.n_steps = n_steps;
+    GB_CHECK(launch_common(h, a, G, st));
+    OuCoef c = make_ou_coef(s);
+    float* Rp = s->R;
+    int64_t ev = every;
+    double* parts = rec ? h->partials : nullptr;
+    void* args[] = {&a, &c, &Rp, &R0, &ev, &parts};
+    GB_CUDA(cudaLaunchCooperativeKernel((const void*)lfg_ou_kernel, dim3((unsigned)G), dim3(256),
+                                        args, 0, st));
+    GB_CHECK(read_status(h, st));
+    h->pos += two_n * n_steps;
+    if (rec) return ou_finish(h, s->n, n_rec, G, mean, corr, st);
+    return GBRNG_OK;
 }
 
 }  // namespace gb

@@ -131,6 +131,12 @@ __global__ void taus_seed_kernel(uint64_t seed, int64_t n, uint4* st)
     st[s] = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+__global__ void lcg_seed_kernel(uint64_t seed, int64_t n, uint32_t* st)
+{
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s < n) st[s] = (uint32_t)splitmix64_at(seed, 8ull * (uint64_t)s);
+}
+
 // Seeding part of Algorithm 2, per stream: idum2 <- idum, NTAB+8 Schrage steps,
 // the last NTAB fill iv[]; iy starts as iv[0].  Layout [35][n].
 __global__ void ran2_seed_kernel(uint64_t seed, int64_t n, int32_t* st)
@@ -158,6 +164,8 @@ static int launch_seed(Handle* h, cudaStream_t st)
         taus_seed_kernel<<<(unsigned)blocks, T, 0, st>>>(h->seed, h->n, h->taus);
     else if (h->kind == GBRNG_RAN2)
         ran2_seed_kernel<<<(unsigned)blocks, T, 0, st>>>(h->seed, h->n, h->r2);
+    else if (h->kind == GBRNG_LCG)
+        lcg_seed_kernel<<<(unsigned)blocks, T, 0, st>>>(h->seed, h->n, h->lcg);
     else
         return lfg_seed(h, st);
     GB_CUDA(cudaGetLastError());
@@ -169,6 +177,7 @@ static void free_handle(Handle* h)
     if (!h) return;
     cudaFree(h->taus);
     cudaFree(h->r2);
+    cudaFree(h->lcg);
     cudaFree(h->ring);
     cudaFree(h->progress);
     cudaFree(h->dstatus);
@@ -185,6 +194,8 @@ static int alloc_state(Handle* h)
         e = cudaMalloc(&h->taus, sizeof(uint4) * h->n);
     } else if (h->kind == GBRNG_RAN2) {
         e = cudaMalloc(&h->r2, sizeof(int32_t) * 35 * h->n);
+    } else if (h->kind == GBRNG_LCG) {
+        e = cudaMalloc(&h->lcg, sizeof(uint32_t) * h->n);
     } else {
         // ring size: power of two >= 2 ll + 2 D + 16384 words.  The leap reads
         // back to p - 2 ll, and a round of W <= 2 D positions overwrites
@@ -211,7 +222,7 @@ static int create(gbrng_t* out, int kind, uint64_t seed, int64_t n, int row, cud
 {
     if (!out) return fail(GBRNG_EINVAL, "out is NULL");
     *out = nullptr;
-    if (kind < GBRNG_TAUS || kind > GBRNG_LAGFIB) return fail(GBRNG_EINVAL, "unknown kind %d", kind);
+    if (kind < GBRNG_TAUS || kind > GBRNG_LCG) return fail(GBRNG_EINVAL, "unknown kind %d", kind);
     if (n < 1) return fail(GBRNG_EINVAL, "n_streams must be >= 1, got %lld", (long long)n);
     if (kind != GBRNG_LAGFIB && n > (int64_t)INT32_MAX * 16)
         return fail(GBRNG_EINVAL, "too many streams");
@@ -391,6 +402,8 @@ int rng_clone(gbrng_t src, gbrng_t* out, void* stream)
     else if (h->kind == GBRNG_RAN2)
         e = cudaMemcpyAsync(h->r2, src->r2, sizeof(int32_t) * 35 * h->n, cudaMemcpyDeviceToDevice,
                             st);
+    else if (h->kind == GBRNG_LCG)
+        e = cudaMemcpyAsync(h->lcg, src->lcg, sizeof(uint32_t) * h->n, cudaMemcpyDeviceToDevice, st);
     else
         e = cudaMemcpyAsync(h->ring, src->ring, sizeof(uint32_t) * ((size_t)h->ring_mask + 1),
                             cudaMemcpyDeviceToDevice, st);
@@ -416,6 +429,7 @@ static size_t payload_bytes(const Handle* h)
 {
     if (h->kind == GBRNG_TAUS) return sizeof(uint32_t) * 4 * (size_t)h->n;
     if (h->kind == GBRNG_RAN2) return sizeof(int32_t) * 35 * (size_t)h->n;
+    if (h->kind == GBRNG_LCG) return sizeof(uint32_t) * (size_t)h->n;
     return sizeof(uint32_t) * (size_t)h->ll;
 }
 
@@ -445,6 +459,8 @@ int rng_get_state(gbrng_t rng, void* host, size_t bytes)
     GB_CUDA(cudaDeviceSynchronize());
     if (rng->kind == GBRNG_TAUS) {
         GB_CUDA(cudaMemcpy(dst, rng->taus, pb, cudaMemcpyDeviceToHost));
+    } else if (rng->kind == GBRNG_LCG) {
+        GB_CUDA(cudaMemcpy(dst, rng->lcg, pb, cudaMemcpyDeviceToHost));
     } else if (rng->kind == GBRNG_RAN2) {
         // device layout [35][n] -> blob [n][35]
         std::vector<int32_t> tmp((size_t)35 * rng->n);
@@ -479,6 +495,8 @@ int rng_set_state(gbrng_t rng, const void* host, size_t bytes)
     GB_CUDA(cudaDeviceSynchronize());
     if (rng->kind == GBRNG_TAUS) {
         GB_CUDA(cudaMemcpy(rng->taus, src, pb, cudaMemcpyHostToDevice));
+    } else if (rng->kind == GBRNG_LCG) {
+        GB_CUDA(cudaMemcpy(rng->lcg, src, pb, cudaMemcpyHostToDevice));
     } else if (rng->kind == GBRNG_RAN2) {
         std::vector<int32_t> tmp((size_t)35 * rng->n);
         const int32_t* in = (const int32_t*)src;
@@ -546,6 +564,24 @@ int ld_run(ld_system* sys, int64_t n_steps, ld_stats* out, void* stream)
     if (n_steps < 0) return fail(GBRNG_EINVAL, "n_steps must be >= 0");
     if (sys->rng->kind == GBRNG_LAGFIB) return lfg_ld(sys, n_steps, 0, out, (cudaStream_t)stream);
     return ld_run_pt(sys, n_steps, out, (cudaStream_t)stream);
+}
+
+int ou_run(ou_system* sys, int64_t n_steps, int64_t every, double* mean, double* corr, void* stream)
+{
+    if (!sys) return fail(GBRNG_EINVAL, "system is NULL");
+    if (sys->n < 1 || !sys->R) return fail(GBRNG_EINVAL, "need n >= 1 and a device array R");
+    if (n_steps < 0 || every < 1) return fail(GBRNG_EINVAL, "need n_steps >= 0 and every >= 1");
+    if (!(sys->k_sp > 0) || !(sys->xi > 0) || !(sys->kT >= 0) || !(sys->dt > 0))
+        return fail(GBRNG_EINVAL, "need k_sp > 0, xi > 0, kT >= 0, dt > 0");
+    if ((mean == nullptr) != (corr == nullptr))
+        return fail(GBRNG_EINVAL, "mean_host and corr_host are both given or both NULL");
+    if (!sys->rng) return fail(GBRNG_EINVAL, "system has no generator");
+    if (sys->rng->kind != GBRNG_LAGFIB && sys->rng->n < sys->n)
+        return fail(GBRNG_EINVAL, "generator has %lld streams for %lld particles",
+                    (long long)sys->rng->n, (long long)sys->n);
+    if (sys->rng->kind == GBRNG_LAGFIB)
+        return lfg_ou(sys, n_steps, every, mean, corr, (cudaStream_t)stream);
+    return ou_run_pt(sys, n_steps, every, mean, corr, (cudaStream_t)stream);
 }
 
 int ld_run_stepwise(ld_system* sys, int64_t n_steps, ld_stats* out, void* stream)

@@ -18,6 +18,7 @@ struct StepArgs {
     LdCoef c;
     uint4* taus;
     int32_t* r2;
+    uint32_t* lcg;
     int64_t S;
     float2* eacc;   // [n] Kahan (sum, compensation) of the oscillator's energy
 };
@@ -37,6 +38,11 @@ __global__ void __launch_bounds__(256) step_pt_kernel(StepArgs a)
         td.y = a.taus[i];
         td.normals3(g0, g1, g2);
         a.taus[i] = td.y;
+    } else if (KIND == GBRNG_LCG) {
+        LcgDraw lc;
+        lc.x = a.lcg[i];
+        lc.normals3(g0, g1, g2);
+        a.lcg[i] = lc.x;
     } else {
         int32_t* r2 = a.r2;
         const int64_t S = a.S;
@@ -114,12 +120,15 @@ int ld_run_stepwise_pt(const ld_system* s, int64_t n_steps, ld_stats* out, cudaS
     a.c = make_coef(s);
     a.taus = h->taus;
     a.r2 = h->r2;
+    a.lcg = h->lcg;
     a.S = h->n;
     a.eacc = h->eacc;
     const unsigned blocks = (unsigned)((s->n + 255) / 256);
     for (int64_t t = 0; t < n_steps; ++t) {
         if (h->kind == GBRNG_TAUS)
             step_pt_kernel<GBRNG_TAUS><<<blocks, 256, 0, st>>>(a);
+        else if (h->kind == GBRNG_LCG)
+            step_pt_kernel<GBRNG_LCG><<<blocks, 256, 0, st>>>(a);
         else
             step_pt_kernel<GBRNG_RAN2><<<blocks, 256, 0, st>>>(a);
     }

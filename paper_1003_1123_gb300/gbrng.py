@@ -16,8 +16,8 @@ import torch
 
 from . import build as _build
 
-TAUS, RAN2, LAGFIB = 0, 1, 2
-_KINDS = {"taus": TAUS, "ran2": RAN2, "lagfib": LAGFIB, "lfg": LAGFIB}
+TAUS, RAN2, LAGFIB, LCG = 0, 1, 2, 3
+_KINDS = {"taus": TAUS, "ran2": RAN2, "lagfib": LAGFIB, "lfg": LAGFIB, "lcg": LCG}
 _STATUS = {0: "GBRNG_OK", -1: "GBRNG_EINVAL", -2: "GBRNG_ENOMEM", -3: "GBRNG_ECUDA",
            -4: "GBRNG_ETIMEOUT", -5: "GBRNG_ELAGS", -6: "GBRNG_ESTATE"}
 
@@ -35,6 +35,11 @@ class LdSystemC(C.Structure):
     _fields_ = [("n", C.c_int64), ("x", C.c_void_p), ("v", C.c_void_p), ("K_per", C.c_void_p),
                 ("K", C.c_double), ("m", C.c_double), ("gamma", C.c_double), ("kT", C.c_double),
                 ("dt", C.c_double), ("rng", C.c_void_p)]
+
+
+class OuSystemC(C.Structure):
+    _fields_ = [("n", C.c_int64), ("R", C.c_void_p), ("k_sp", C.c_double), ("xi", C.c_double),
+                ("kT", C.c_double), ("dt", C.c_double), ("rng", C.c_void_p)]
 
 
 class LdStatsC(C.Structure):
@@ -71,6 +76,8 @@ SIGNATURES = {
     "ld_run": (C.c_int, [C.POINTER(LdSystemC), C.c_int64, C.POINTER(LdStatsC), C.c_void_p]),
     "ld_run_stepwise": (C.c_int, [C.POINTER(LdSystemC), C.c_int64, C.POINTER(LdStatsC),
                                   C.c_void_p]),
+    "ou_run": (C.c_int, [C.POINTER(OuSystemC), C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
+                         C.c_void_p]),
     "ld_run_batched": (C.c_int, [C.POINTER(LdSystemC), C.c_int, C.c_int64,
                                  C.POINTER(C.c_int), C.POINTER(LdStatsC), C.c_void_p]),
     "ld_backward": (C.c_int, [C.POINTER(LdSystemC), C.c_int64, C.c_int, C.c_void_p,
@@ -326,3 +333,33 @@ def ld_backward(system: LdSystem, n_steps: int, ckpt_every: int = 100, dK: torch
     _check(lib().ld_backward(C.byref(cs), n_steps, ckpt_every, _ptr(dK), C.byref(dg),
                              C.byref(dk), C.byref(loss), _stream(stream)))
     return {"loss": loss.value, "dgamma": dg.value, "dkT": dk.value, "dK": dK}
+
+
+# ------------------------------------------------------ overdamped 1-D runs
+class OuSystem:
+    """n 1-D particles (Eq. 4-5): R is a float32 [n] CUDA tensor."""
+
+    def __init__(self, rng: Rng, R: torch.Tensor, k_sp=1.0, xi=1.0, kT=1.0, dt=0.01):
+        assert R.is_cuda and R.dtype == torch.float32 and R.is_contiguous() and R.dim() == 1
+        self.rng, self.R = rng, R
+        self.k_sp, self.xi, self.kT, self.dt = float(k_sp), float(xi), float(kT), float(dt)
+
+    def c_struct(self) -> OuSystemC:
+        return OuSystemC(self.R.numel(), self.R.data_ptr(), self.k_sp, self.xi, self.kT, self.dt,
+                         self.rng.handle)
+
+
+def ou_run(system: OuSystem, n_steps: int, every: int = 0, stream=None):
+    """Advance by n_steps; with every >= 1 returns (mean, corr) numpy arrays of
+    n_steps // every + 1 records (<R(t)> and <R(t)R(0)>), else None."""
+    import numpy as np
+    cs = system.c_struct()
+    if every:
+        n_rec = n_steps // every + 1
+        mean = np.zeros(n_rec, np.float64)
+        corr = np.zeros(n_rec, np.float64)
+        _check(lib().ou_run(C.byref(cs), n_steps, every, mean.ctypes.data, corr.ctypes.data,
+                            _stream(stream)))
+        return mean, corr
+    _check(lib().ou_run(C.byref(cs), n_steps, 1, None, None, _stream(stream)))
+    return None

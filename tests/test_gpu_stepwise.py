@@ -36,7 +36,7 @@ def pair(G, kind, n, seed, row=None, kper=False):
     return out
 
 
-@pytest.mark.parametrize("kind,n,row", [("taus", 5000, None), ("ran2", 3001, None),
+@pytest.mark.parametrize("kind,n,row", [("taus", 5000, None), ("ran2", 3001, None), ("lcg", 999, None),
                                         ("lagfib", 4096, None), ("lagfib", 600, 3),
                                         ("lagfib", 100, 0)])
 def test_stepwise_equals_persistent(G, kind, n, row):
