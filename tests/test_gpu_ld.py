@@ -237,6 +237,38 @@ def test_lagfib_timeout_reported_without_fault(G):
     assert G.rng_fill_u32(r2, 10**6).numel() == 10**6
 
 
+@pytest.mark.parametrize("path", ["resident", "fill", "ou"])
+def test_lagfib_timeouts_on_every_cooperative_kernel(G, path):
+    """The stall hook (one CTA never arrives at the grid barrier) ends the
+    resident-state fused kernel, the fill rounds and the overdamped run with
+    GBRNG_ETIMEOUT after the wait limit; the context stays usable."""
+    n = 10**5
+    r = G.rng_init("lagfib", 9, n)
+    x = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    s = G.LdSystem(r, x, torch.zeros_like(x))
+    G.ld_init_equilibrium(s)
+    G.rng_fill_u32(r, 4 * 10**6)           # past ll: the fused run takes the resident kernel
+    G.rng_set_wait_limit_ns(200_000_000)
+    G.gbrng_test_stall_chunk(5)
+    try:
+        with pytest.raises(G.GbrngError) as e:
+            if path == "resident":
+                G.ld_run(s, 20, stats=False)
+            elif path == "fill":
+                G.rng_fill_uniform(r, 32 * 10**6)
+            else:
+                ro = G.rng_init("lagfib", 9, 1000)
+                G.ou_run(G.OuSystem(ro, torch.zeros(1000, dtype=torch.float32, device="cuda")),
+                         50, 10)
+        assert e.value.code == -4
+    finally:
+        G.gbrng_test_stall_chunk(-1)
+        G.rng_set_wait_limit_ns(2_000_000_000)
+    torch.cuda.synchronize()
+    r2 = G.rng_init("lagfib", 1, 100)
+    assert G.rng_fill_u32(r2, 10**6).numel() == 10**6
+
+
 def test_zero_steps_and_empty(G):
     s, _, _ = make_pair(G, "taus", 100, 1)
     G.ld_init_equilibrium(s)
