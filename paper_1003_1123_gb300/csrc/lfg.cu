@@ -347,10 +347,12 @@ __global__ void __launch_bounds__(kLfgThreads, MODE == LFG_LD ? 1 : 2) lfg_kerne
 }
 
 // ------------------------------------------------- fused step, resident state
-// When every step of the launch is one all-leap round (4N <= the round width
+// When every step of the launch fits an all-leap round (4N <= the round width
 // and the launch starts at or above ll), CTA c owns the oscillators
 // [c n_c, c n_c + n_c) for the whole launch and keeps their x and v in shared
-// memory: a step's global traffic is then the ring alone.  A step's positions
+// memory: a step's global traffic is then the ring alone.  A round holds
+// floor(width / 4N) steps, since an oscillator's consecutive steps stay with
+// one lane and only the ring is shared.  A step's positions
 // for the CTA are one contiguous region; when none of its windows wraps around
 // the ring (all but about one step in R / 4N), each lane addresses the region
 // with one pointer per window and the blocks are walked two at a time, the
@@ -378,6 +380,10 @@ __global__ void __launch_bounds__(kResThreads, 1) lfg_resident_kernel(LfgArgs a,
     uint32_t* buf = bufs[warp];
     Kahan e;
     double acc[3] = {0, 0, 0};
+    // kr steps per round: their 4 N kr positions read only earlier rounds, and
+    // each oscillator's steps stay with one lane, so no barrier is needed
+    // inside a round
+    const int64_t kr = max((int64_t)1, a.w_leap / (4 * a.N));
     for (int64_t t = 0; t < a.n_steps; ++t) {
         const bool last = t == a.n_steps - 1;
         // oscillator jj of this CTA from its four values w
@@ -445,7 +451,8 @@ __global__ void __launch_bounds__(kResThreads, 1) lfg_resident_kernel(LfgArgs a,
                 if (4 * lane < nval) osc(32 * (int)b + lane, w);
             });
         }
-        if (!last && !grid_barrier(a, (uint32_t)gridDim.x * (uint32_t)(t + 1), arrive_here))
+        if (!last && (t + 1) % kr == 0 &&
+            !grid_barrier(a, (uint32_t)gridDim.x * (uint32_t)((t + 1) / kr), arrive_here))
             return;
     }
     __syncthreads();
@@ -657,6 +664,8 @@ static int try_launch_resident(Handle* h, LfgArgs& a, cudaStream_t st, int64_t* 
     if (occ < 1) return 0;
     GB_CHECK(ensure_partials(h, G));
     a.partials = h->partials;
+    int64_t w_base_full = 0;
+    round_widths(h, 0, &w_base_full, &a.w_leap);   // the full leap width: several steps a round
     GB_CHECK(launch_common(h, a, G, st));
     int64_t nc_arg = n_c;
     void* args[] = {&a, &nc_arg};
