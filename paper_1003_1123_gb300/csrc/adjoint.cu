@@ -45,8 +45,12 @@ struct AdjArgs {
     double* partials;   // [grid][4]: loss, dgamma, dkT, unused
 };
 
+// 64-thread blocks with a 72-register budget: fourteen blocks per SM, so 1e5
+// oscillators fit one resident wave with one oscillator per thread and the
+// SMs differ by at most one block (at 96 registers and 128 threads the same
+// system needed two oscillators per thread on 2.6 blocks per SM).
 template <int KIND>
-__global__ void __launch_bounds__(128) adjoint_kernel(AdjArgs a)
+__global__ void __launch_bounds__(64, 14) adjoint_kernel(AdjArgs a)
 {
     extern __shared__ int32_t tab[];   // Ran2: [32][blockDim.x]
     __shared__ double red[4 * 32];
@@ -258,16 +262,15 @@ extern "C" int ld_backward(ld_system* sys, int64_t n_steps, int ckpt_every, floa
     }
     DevInfo di;
     GB_CHECK(dev_info(h->device, &di));
-    const int T = 128;
+    const int T = 64;
     const size_t smem = h->kind == GBRNG_RAN2 ? sizeof(int32_t) * 32 * T : 0;
     int occ = 0;
     cudaError_t e = h->kind == GBRNG_TAUS
         ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel<GBRNG_TAUS>, T, smem)
         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, adjoint_kernel<GBRNG_RAN2>, T, smem);
     if (e != cudaSuccess || occ < 1) occ = 1;
-    const int64_t wave = (int64_t)di.sms * occ * T;
-    const int64_t per_thread = (n + wave - 1) / wave;
-    const int64_t blocks = (n + per_thread * T - 1) / (per_thread * T);
+    // one full resident wave at most; oscillators i, i + W, ... per thread
+    const int64_t blocks = std::min<int64_t>((int64_t)di.sms * occ, (n + T - 1) / T);
     int rc = ensure_partials(h, blocks);
     if (rc != GBRNG_OK) {
         cudaFreeAsync(scratch, st);
