@@ -130,3 +130,29 @@ def test_ou_paper_relaxation_and_correlation(G, kind):
         e = math.exp(-k * every * PAPER["dt"] / TAU)
         sd = var_eq * math.sqrt((1 + e * e) / n)
         assert abs(c - var_eq * e) <= 4 * sd, (k, c)
+
+
+@pytest.mark.parametrize("kind", ["taus", "lagfib"])
+def test_ou_edge_cases(G, kind):
+    """Zero steps record only the entry state; every > n_steps gives one record;
+    n_steps = 0 without records leaves R and the generator untouched; bad
+    arguments are rejected before any work."""
+    n = 300
+    r = G.rng_init(kind, 2, n)
+    R0 = torch.linspace(-1, 1, n, dtype=torch.float32, device="cuda")
+    s = G.OuSystem(r, R0.clone())
+    before = G.rng_get_state(r)
+    mean, corr = G.ou_run(s, 0, 5)
+    assert len(mean) == 1 and mean[0] == pytest.approx(float(R0.double().mean()), abs=1e-12)
+    assert corr[0] == pytest.approx(float((R0.double() ** 2).mean()), rel=1e-12)
+    assert G.rng_get_state(r) == before and torch.equal(s.R, R0)
+    mean, corr = G.ou_run(s, 7, 100)
+    assert len(mean) == 1
+    with pytest.raises(G.GbrngError):
+        G.ou_run(G.OuSystem(r, R0.clone(), k_sp=-1.0), 5, 1)
+    with pytest.raises(G.GbrngError):
+        G.ou_run(G.OuSystem(r, R0.clone(), dt=0.0), 5, 1)
+    small = G.rng_init("taus", 2, 10)
+    if kind == "taus":
+        with pytest.raises(G.GbrngError):      # fewer streams than particles
+            G.ou_run(G.OuSystem(small, R0.clone()), 5, 1)
