@@ -36,7 +36,7 @@ namespace gb {
 
 enum { LFG_U32 = 0, LFG_UNIFORM = 1, LFG_NORMAL = 2, LFG_LD = 3, LFG_LD_INIT = 4 };
 
-constexpr int kLfgThreads = 512;
+constexpr int kLfgThreads = 256;   // three CTAs per SM (80 registers): 24 warps to hide HBM latency
 constexpr int kLfgWarps = kLfgThreads / 32;
 constexpr int kLfgDepth = 2;     // blocks per warp with lag loads in flight
 
@@ -253,7 +253,7 @@ __device__ __forceinline__ void em_update(const LdCoef& c, float Ki, float g0, f
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kLfgThreads, MODE == LFG_LD ? 1 : 2) lfg_kernel(LfgArgs a)
+__global__ void __launch_bounds__(kLfgThreads, 3) lfg_kernel(LfgArgs a)
 {
     __shared__ __align__(16) uint32_t bufs[kLfgWarps][128];
     __shared__ double red[4 * 32];
