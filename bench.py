@@ -300,7 +300,8 @@ def run_gpu(args, rank, world, dist):
                    "params": PARAMS, "l2": "flushed (256 MiB write) before every part",
                    "parallelism": f"replicas x{world} (independent seeds, no collective)"},
         "clocks": clk,
-        "gpu_launches": gpu_launches(parts, args.steps),
+        "gpu_launches": gpu_launches(parts, args.steps, G.ld_batched_tune(wl.batch)),
+        "batched_tune": list(G.ld_batched_tune(wl.batch)),
         "e2e": e2e,
         "roofline": roof,
         "parts": per_part,
@@ -311,15 +312,17 @@ def run_gpu(args, rank, world, dist):
     return line
 
 
-def gpu_launches(parts, steps):
+def gpu_launches(parts, steps, batched_tune=None):
     """Kernels of ours launched per timed step: one persistent kernel per fused
-    run plus the statistics finisher, one kernel per fill."""
+    run plus the statistics finisher, one kernel per fill, and for the batched
+    graph ceil(steps / L) persistent launches plus the per-system reduction."""
     n = 0
     for name, _, _ in parts:
         if name.startswith("ld_") or name.startswith("adjoint"):
             n += 2                  # persistent kernel + statistics finisher
         elif name.startswith("batched"):
-            n += 2                  # graph: one persistent launch + per-system reduction
+            L = batched_tune[2] if batched_tune else 0
+            n += (-(-BATCH_STEPS // L) if L > 0 else 1) + 1
         else:
             n += 1
     return n * steps

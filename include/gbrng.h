@@ -250,6 +250,14 @@ int ld_run_stepwise(ld_system* sys, int64_t n_steps, ld_stats* out_host, void* s
 int ld_run_batched(ld_system* sys, int n_sys, int64_t n_steps, const int* tune,
                    ld_stats* out, void* stream);
 
+/* The launch shape the autotuner chose for these systems' shape (their kinds
+ * and sizes), as tune_out = {threads per block, oscillators per thread, steps
+ * per launch (0: all steps in one launch)}; GBRNG_EINVAL if that shape has not
+ * been autotuned in this process or read from $GBRNG_TUNE_CACHE.  Runs nothing
+ * (an introspection call: one replay of the graph launches ceil(steps / L)
+ * persistent kernels and one reduction). */
+int ld_batched_tune(const ld_system* sys, int n_sys, int* tune_out);
+
 /* Reverse-time adjoint of L = (1/S) sum_{t=1..S} E(t) (S = n_steps) under the
  * fixed noise of the generator, starting from the system's current state.
  * Generator states and (x, v) are checkpointed every ckpt_every steps; the

@@ -515,3 +515,22 @@ extern "C" int ld_run_batched(ld_system* sys, int n_sys, int64_t n_steps, const 
     }
     return GBRNG_OK;
 }
+
+extern "C" int ld_batched_tune(const ld_system* sys, int n_sys, int* tune_out)
+{
+    if (!sys || n_sys < 1 || !tune_out) return fail(GBRNG_EINVAL, "NULL argument or no systems");
+    const int kind = sys[0].rng ? sys[0].rng->kind : -1;
+    if (kind != GBRNG_TAUS && kind != GBRNG_RAN2)
+        return fail(GBRNG_EINVAL, "batched systems need per-thread generators (Taus or Ran2)");
+    std::vector<int64_t> sizes(n_sys);
+    for (int s = 0; s < n_sys; ++s) sizes[s] = sys[s].n;
+    const std::string key = shape_key(sys[0].rng->device, kind, sizes);
+    std::lock_guard<std::mutex> lk(g_mu);
+    load_tune_cache();
+    auto it = g_tuned.find(key);
+    if (it == g_tuned.end()) return fail(GBRNG_EINVAL, "this shape has not been autotuned yet");
+    tune_out[0] = it->second.T;
+    tune_out[1] = it->second.K;
+    tune_out[2] = (int)it->second.L;
+    return GBRNG_OK;
+}

@@ -80,6 +80,7 @@ SIGNATURES = {
                          C.c_void_p]),
     "ld_run_batched": (C.c_int, [C.POINTER(LdSystemC), C.c_int, C.c_int64,
                                  C.POINTER(C.c_int), C.POINTER(LdStatsC), C.c_void_p]),
+    "ld_batched_tune": (C.c_int, [C.POINTER(LdSystemC), C.c_int, C.POINTER(C.c_int)]),
     "ld_backward": (C.c_int, [C.POINTER(LdSystemC), C.c_int64, C.c_int, C.c_void_p,
                               C.POINTER(C.c_double), C.POINTER(C.c_double),
                               C.POINTER(C.c_double), C.c_void_p]),
@@ -321,6 +322,14 @@ def ld_run_batched(systems, n_steps: int, tune=None, stats: bool = True, stream=
     _check(lib().ld_run_batched(arr, len(systems), n_steps, tn, out if stats else None,
                                 _stream(stream)))
     return [_stats(s) for s in out] if stats else None
+
+
+def ld_batched_tune(systems):
+    """The autotuned (T, K, steps per launch) of these systems' shape."""
+    arr = (LdSystemC * len(systems))(*[s.c_struct() for s in systems])
+    out = (C.c_int * 3)()
+    _check(lib().ld_batched_tune(arr, len(systems), out))
+    return tuple(out)
 
 
 def ld_backward(system: LdSystem, n_steps: int, ckpt_every: int = 100, dK: torch.Tensor = None,

@@ -124,3 +124,15 @@ def test_batched_paper_shaped_workload(G):
         S = oracle.em_covariance(sp["K"], sp["m"], sp["gamma"], sp["kT"], sp["dt"], steps)
         cnt = 3 * sp["n"]
         assert abs(s["sum_x2"] / cnt - S[0, 0]) < 5 * S[0, 0] * math.sqrt(2 / cnt)
+
+
+def test_batched_tune_introspection(G):
+    """ld_batched_tune reports the autotuned shape once a shape has been tuned
+    and refuses (without running anything) before that."""
+    specs = W.batched_systems(5, seed=77, n_lo=50, n_hi=700)
+    a = make_systems(G, "taus", specs)
+    with pytest.raises(G.GbrngError):
+        G.ld_batched_tune(a)
+    G.ld_run_batched(a, 20)
+    T, K, L = G.ld_batched_tune(a)
+    assert T in range(32, 257, 32) and K in (1, 2) and L >= 0
