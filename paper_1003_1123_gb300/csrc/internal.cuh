@@ -51,7 +51,7 @@ struct Handle {
     int64_t pos = 0;           // next position to generate
 
     // scratch owned by the handle
-    uint32_t* progress = nullptr;   // grid-barrier arrival counter (LFG)
+    uint64_t* progress = nullptr;   // grid-barrier arrival counter (LFG)
     int64_t progress_cap = 0;
     int* dstatus = nullptr;         // device status word
     double* partials = nullptr;     // per-block reduction partials

@@ -56,7 +56,7 @@ struct LfgArgs {
     float* v;
     const float* Kper;
     LdCoef c;
-    uint32_t* arrive;      // grid-barrier arrival counter (zeroed before launch)
+    uint64_t* arrive;      // grid-barrier arrival counter (zeroed before launch; 64-bit, never wraps)
     int* status;
     uint64_t wait_ns;
     double* partials;      // [G][4]
@@ -68,15 +68,15 @@ struct LfgArgs {
 // every CTA of this round has arrived, then fences (acquire).  The poll is
 // bounded by a %globaltimer deadline and stops early when another CTA has
 // recorded a failure.  Returns false on every thread of the CTA on failure.
-__device__ bool grid_barrier(const LfgArgs& a, uint32_t target, bool arrive_here)
+__device__ bool grid_barrier(const LfgArgs& a, uint64_t target, bool arrive_here)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        if (arrive_here) red_release_add_u32(a.arrive, 1u);
+        if (arrive_here) red_release_add_u64(a.arrive, 1ull);
         const uint64_t deadline = global_ns() + a.wait_ns;
-        for (uint32_t n = 1; ld_relaxed_u32(a.arrive) < target; ++n) {
+        for (uint32_t n = 1; ld_relaxed_u64(a.arrive) < target; ++n) {
             if ((n & 15u) == 0) {
                 if (ld_volatile_i32(a.status) != DEV_OK) {
                     ok = 0;
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kLfgThreads, 3) lfg_kernel(LfgArgs a)
     const bool arrive_here = (int)blockIdx.x != a.stall_cta;
     Kahan e;
     double acc[3] = {0, 0, 0};
-    uint32_t round = 0;
+    uint64_t round = 0;
     for (int64_t U = 0; U < a.n_pos; ++round) {
         // rounds: whole oscillator-steps for the fused step (U, widths are multiples of 4)
         const int64_t wpos = a.base + U >= a.ll ? a.w_leap : a.w_base;
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kLfgThreads, 3) lfg_kernel(LfgArgs a)
                         });
         }
         U = U1;
-        if (U < a.n_pos && !grid_barrier(a, (uint32_t)gridDim.x * (round + 1), arrive_here)) return;
+        if (U < a.n_pos && !grid_barrier(a, (uint64_t)gridDim.x * (round + 1), arrive_here)) return;
     }
     if (MODE == LFG_LD && a.partials) {
         double v[4] = {acc[0], acc[1], acc[2], e.value()};
@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(kResThreads, 1) lfg_resident_kernel(LfgArgs a,
             });
         }
         if (!last && (t + 1) % kr == 0 &&
-            !grid_barrier(a, (uint32_t)gridDim.x * (uint32_t)((t + 1) / kr), arrive_here))
+            !grid_barrier(a, (uint64_t)gridDim.x * (uint64_t)((t + 1) / kr), arrive_here))
             return;
     }
     __syncthreads();
@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(256) lfg_ou_kernel(LfgArgs a, OuCoef c, float*
             R[j] = __fmaf_rn(c.cs, g, __fmaf_rn(-c.c1, R[j], R[j]));
         }
         if (t + 1 < a.n_steps &&
-            !grid_barrier(a, (uint32_t)gridDim.x * (uint32_t)(t + 1), arrive_here))
+            !grid_barrier(a, (uint64_t)gridDim.x * (uint64_t)(t + 1), arrive_here))
             return;
     }
 }
@@ -611,7 +611,7 @@ static int launch_common(Handle* h, LfgArgs& a, int64_t G, cudaStream_t st)
     a.status = h->dstatus;
     a.wait_ns = wait_limit_ns();
     a.stall_cta = test_stall_chunk() < 0 ? -1 : (int)(test_stall_chunk() % G);
-    GB_CUDA(cudaMemsetAsync(h->progress, 0, sizeof(uint32_t), st));
+    GB_CUDA(cudaMemsetAsync(h->progress, 0, sizeof(uint64_t), st));
     GB_CUDA(cudaMemsetAsync(h->dstatus, 0, sizeof(int), st));
     return GBRNG_OK;
 }

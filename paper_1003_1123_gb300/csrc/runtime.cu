@@ -86,7 +86,7 @@ int ensure_progress(Handle* h, int64_t count)
     if (h->progress) cudaFree(h->progress);
     h->progress = nullptr;
     h->progress_cap = 0;
-    if (cudaMalloc(&h->progress, sizeof(uint32_t) * count) != cudaSuccess) {
+    if (cudaMalloc(&h->progress, sizeof(uint64_t) * count) != cudaSuccess) {
         cudaGetLastError();
         return fail(GBRNG_ENOMEM, "cannot allocate %lld progress counters", (long long)count);
     }
