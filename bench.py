@@ -472,44 +472,76 @@ def roofline(part, ms, units, peaks, src, clk, l2_gbs=None):
 
 
 # --------------------------------------------------------------------- CPU
-def _oracle_rates(budget_scale=1.0):
-    """Time the oracle as it stands (one host core) on bounded samples of the
-    workload; returns per-part rates."""
+ORACLE_PARTS = ("ld_taus", "ld_ran2", "ld_lagfib", "fill_uniform_taus", "fill_normal_taus",
+                "fill_uniform_ran2", "fill_normal_ran2", "fill_uniform_lagfib",
+                "fill_normal_lagfib", "adjoint_taus")
+
+
+def _oracle_part(name: str, scale: float, shard: int = 0):
+    """One bounded sample of one part on the oracle as it stands, in this
+    process; returns (units done, seconds).  Shards of the per-thread kinds use
+    disjoint seeds (the oracle's streams are independent)."""
     import numpy as np
     import oracle
     p = oracle.params(**PARAMS)
-    rates = {}
-    n_pt, steps_pt = int(20000 * budget_scale), 100
-    for kind in KINDS:
+    seed = SEED + 1009 * shard
+    kind = name.split("_")[-1]
+    if name.startswith("ld_"):
         if kind == "lagfib":
-            g = oracle.Gen(kind, SEED, N_OSC)
+            g = oracle.Gen(kind, seed, N_OSC)
             x, v = oracle.ld_init_eq_f32(g, N_OSC, p)
-            steps = max(1, int(2 * budget_scale))
+            steps = max(1, int(2 * scale))
             t0 = time.perf_counter()
             oracle.ld_run_f32(g, x, v, p, steps)
-            rates[f"ld_{kind}"] = N_OSC * steps / (time.perf_counter() - t0)
-        else:
-            g = oracle.Gen(kind, SEED, n_pt)
-            x, v = oracle.ld_init_eq_f32(g, n_pt, p)
-            t0 = time.perf_counter()
-            oracle.ld_run_f32(g, x, v, p, steps_pt)
-            rates[f"ld_{kind}"] = n_pt * steps_pt / (time.perf_counter() - t0)
-        nf = int(2 * 10**6 * budget_scale)
-        g = oracle.Gen(kind, SEED + 7, N_OSC if kind == "lagfib" else 4096)
+            return N_OSC * steps, time.perf_counter() - t0
+        n, steps = int(20000 * scale), 100
+        g = oracle.Gen(kind, seed, n)
+        x, v = oracle.ld_init_eq_f32(g, n, p)
         t0 = time.perf_counter()
-        g.fill_uniform(nf)
-        rates[f"fill_uniform_{kind}"] = nf / (time.perf_counter() - t0)
+        oracle.ld_run_f32(g, x, v, p, steps)
+        return n * steps, time.perf_counter() - t0
+    if name.startswith("fill_"):
+        nf = int(2 * 10**6 * scale)
+        g = oracle.Gen(kind, seed + 7, N_OSC if kind == "lagfib" else 4096)
+        f = g.fill_uniform if "uniform" in name else g.fill_normal
         t0 = time.perf_counter()
-        g.fill_normal(nf)
-        rates[f"fill_normal_{kind}"] = nf / (time.perf_counter() - t0)
-    # batched systems run the same per-oscillator arithmetic as a Taus system
-    rates["batched_taus"] = rates["ld_taus"]
-    na, sa = max(8, int(200 * budget_scale)), 1000
-    g = oracle.Gen("taus", SEED + 11, na)
+        f(nf)
+        return nf, time.perf_counter() - t0
+    na, sa = max(8, int(200 * scale)), 1000          # adjoint_taus, FP64
+    g = oracle.Gen("taus", seed + 11, na)
     x, v = oracle.ld_init_eq_f64(g, na, p)
     t0 = time.perf_counter()
     oracle.ld_adjoint_f64(g, x, v, p, sa, Kper=np.ones(na))
-    rates["adjoint_taus"] = na * sa / (time.perf_counter() - t0)
+    return na * sa, time.perf_counter() - t0
+
+
+def oracle_pool(workers: int):
+    """A process pool for the oracle, started with spawn (no inherited CUDA
+    state), or None for one core."""
+    if workers <= 1:
+        return None
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    return cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+
+
+def _oracle_rates(budget_scale=1.0, pool=None, workers=1):
+    """Time the oracle as it stands on bounded samples of the workload; returns
+    per-part rates.  With a pool, each per-thread part runs `workers` shards at
+    once and its rate is their units over the wall time; the Lagged Fibonacci
+    sequence is serial by definition and stays on one core."""
+    rates = {}
+    for name in ORACLE_PARTS:
+        if pool is None or name.endswith("lagfib"):
+            units, sec = _oracle_part(name, budget_scale)
+            rates[name] = units / sec
+            continue
+        t0 = time.perf_counter()
+        futs = [pool.submit(_oracle_part, name, budget_scale, k) for k in range(workers)]
+        units = sum(f.result()[0] for f in futs)
+        rates[name] = units / (time.perf_counter() - t0)
+    # batched systems run the same per-oscillator arithmetic as a Taus system
+    rates["batched_taus"] = rates["ld_taus"]
     return rates
 
 
@@ -531,36 +563,51 @@ def _cpu_step_seconds(rates):
     return sum(units[name] / r for name, r in rates.items())
 
 
-def _sample_text(scale):
+def _sample_text(scale, workers=1):
+    per = f" in each of {workers} concurrent processes (Lagged Fibonacci on one)" if workers > 1 else ""
     return (f"per generator: Taus/Ran2 {int(20000 * scale)} oscillators x 100 steps, Lagged "
             f"Fibonacci all 1e6 oscillators x {max(1, int(2 * scale))} steps, "
             f"{int(2e6 * scale)} uniform + {int(2e6 * scale)} normal fill numbers, "
-            f"FP64 adjoint of {max(8, int(200 * scale))} oscillators x 1000 steps (batched "
+            f"FP64 adjoint of {max(8, int(200 * scale))} oscillators x 1000 steps{per} (batched "
             f"systems at the Taus rate); extrapolated per unit to the full step")
 
 
 def cpu_baseline(parts, part_ms, steps):
-    rates = _oracle_rates(1.0)
-    sec = _cpu_step_seconds(rates)
-    return {"value": _step_osc_steps(_step_units()) / sec, "unit": "oscillator-steps/s", "cores": 1,
-            "kind": "oracle", "sample": _sample_text(1.0),
-            "parts": {k: v for k, v in rates.items()}}
+    """The oracle on all host cores (spawned processes over independent
+    streams), and on one core for reference."""
+    workers = os.cpu_count() or 1
+    pool = oracle_pool(workers)
+    try:
+        rates = _oracle_rates(1.0, pool, workers)
+    finally:
+        if pool:
+            pool.shutdown()
+    one = _oracle_rates(1.0)
+    units = _step_osc_steps(_step_units())
+    return {"value": units / _cpu_step_seconds(rates), "unit": "oscillator-steps/s",
+            "cores": workers, "kind": "oracle", "sample": _sample_text(1.0, workers),
+            "parts": {k: v for k, v in rates.items()},
+            "one_core": {"value": units / _cpu_step_seconds(one), "cores": 1,
+                         "parts": {k: v for k, v in one.items()}}}
 
 
 def run_reference(args, world):
     """The oracle on the host cores, timed like our arm: W untimed and K timed
     steps, each a bounded sample of the workload extrapolated per unit."""
     scale = 0.5
-    for _ in range(args.warmup):
-        _oracle_rates(0.1)
-    secs = []
-    t0 = time.perf_counter()
-    all_rates = []
-    for _ in range(args.steps):
-        rates = _oracle_rates(scale)
-        all_rates.append(rates)
-        secs.append(_cpu_step_seconds(rates))
-    wall = time.perf_counter() - t0
+    workers = os.cpu_count() or 1
+    pool = oracle_pool(workers)
+    try:
+        for _ in range(args.warmup):
+            _oracle_rates(0.1, pool, workers)
+        secs = []
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            secs.append(_cpu_step_seconds(_oracle_rates(scale, pool, workers)))
+        wall = time.perf_counter() - t0
+    finally:
+        if pool:
+            pool.shutdown()
     ms_per_step = 1e3 * statistics.mean(secs)
     value = _step_osc_steps(_step_units()) / (ms_per_step / 1e3)
     return {
@@ -571,8 +618,8 @@ def run_reference(args, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+u32",
         "data": "synthetic (seeded oscillators; equilibrium start)",
         "config": {"workload": WORKLOAD, "timed_wall_s": wall},
-        "cpu_baseline": {"value": value, "unit": "oscillator-steps/s", "cores": 1,
-                         "kind": "oracle", "sample": _sample_text(scale)},
+        "cpu_baseline": {"value": value, "unit": "oscillator-steps/s", "cores": workers,
+                         "kind": "oracle", "sample": _sample_text(scale, workers)},
         "e2e": {"value": value, "unit": "oscillator-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
