@@ -236,6 +236,7 @@ using namespace gb;
 extern "C" int ld_backward(ld_system* sys, int64_t n_steps, int ckpt_every, float* dK_per,
                            double* dgamma, double* dkT, double* loss, void* stream)
 {
+    NvtxRange range("ld_backward");
     GB_CHECK(check_system(sys, true));
     Handle* h = sys->rng;
     if (h->kind != GBRNG_TAUS && h->kind != GBRNG_RAN2)

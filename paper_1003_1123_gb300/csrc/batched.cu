@@ -447,6 +447,7 @@ using namespace gb;
 extern "C" int ld_run_batched(ld_system* sys, int n_sys, int64_t n_steps, const int* tune,
                               ld_stats* out, void* stream)
 {
+    NvtxRange range("ld_run_batched");
     if (!sys || n_sys < 1) return fail(GBRNG_EINVAL, "need at least one system");
     if (n_steps < 0) return fail(GBRNG_EINVAL, "n_steps must be >= 0");
     const int kind = sys[0].rng ? sys[0].rng->kind : -1;

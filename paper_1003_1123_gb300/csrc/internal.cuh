@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cstdio>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "gbrng.h"
 
 namespace gb {
@@ -30,6 +32,15 @@ void clear_error();
 
 // Status values written by kernels into the handle's device status word.
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1 };
+
+// NVTX range named after the C ABI call, open for the call's duration (a
+// no-op unless a profiler or tracer is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // ---------------------------------------------------------------- handle
 struct Handle {

@@ -150,6 +150,7 @@ using namespace gb;
 
 extern "C" int ld_run_noalloc(ld_system* sys, int64_t n_steps, ld_stats* out_host, void* stream)
 {
+    NvtxRange range("ld_run_noalloc");
     GB_CHECK(check_system(sys, true));
     if (n_steps < 0) return fail(GBRNG_EINVAL, "n_steps must be >= 0");
     Handle* h = sys->rng;

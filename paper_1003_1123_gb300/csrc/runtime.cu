@@ -351,11 +351,13 @@ int rng_lfg_default_row(int64_t n_threads)
 
 int rng_init(gbrng_t* out, int kind, uint64_t seed, int64_t n_streams, void* stream)
 {
+    NvtxRange range("rng_init");
     return create(out, kind, seed, n_streams, -1, (cudaStream_t)stream);
 }
 
 int rng_init_lfg(gbrng_t* out, uint64_t seed, int64_t n_threads, int lag_row, void* stream)
 {
+    NvtxRange range("rng_init_lfg");
     if (lag_row < -1 || lag_row > 9) {
         if (out) *out = nullptr;
         return fail(GBRNG_ELAGS, "lag_row must be -1 or 0-9, got %d", lag_row);
@@ -442,6 +444,7 @@ int rng_state_bytes(gbrng_t rng, size_t* bytes)
 
 int rng_get_state(gbrng_t rng, void* host, size_t bytes)
 {
+    NvtxRange range("rng_get_state");
     if (!rng || !host) return fail(GBRNG_EINVAL, "NULL argument");
     const size_t pb = payload_bytes(rng);
     if (bytes != sizeof(gbrng_state_header) + pb)
@@ -481,6 +484,7 @@ int rng_get_state(gbrng_t rng, void* host, size_t bytes)
 
 int rng_set_state(gbrng_t rng, const void* host, size_t bytes)
 {
+    NvtxRange range("rng_set_state");
     if (!rng || !host) return fail(GBRNG_EINVAL, "NULL argument");
     const size_t pb = payload_bytes(rng);
     if (bytes != sizeof(gbrng_state_header) + pb)
@@ -526,6 +530,7 @@ int rng_set_state(gbrng_t rng, const void* host, size_t bytes)
 
 int rng_fill_u32(gbrng_t rng, uint32_t* dst, int64_t n, void* stream)
 {
+    NvtxRange range("rng_fill_u32");
     if (!rng || (n > 0 && !dst) || n < 0) return fail(GBRNG_EINVAL, "bad fill arguments");
     if (n == 0) return GBRNG_OK;
     if (rng->kind == GBRNG_LAGFIB) return lfg_fill(rng, dst, n, 0, (cudaStream_t)stream);
@@ -534,6 +539,7 @@ int rng_fill_u32(gbrng_t rng, uint32_t* dst, int64_t n, void* stream)
 
 int rng_fill_uniform(gbrng_t rng, float* dst, int64_t n, void* stream)
 {
+    NvtxRange range("rng_fill_uniform");
     if (!rng || (n > 0 && !dst) || n < 0) return fail(GBRNG_EINVAL, "bad fill arguments");
     if (n == 0) return GBRNG_OK;
     if (rng->kind == GBRNG_LAGFIB) return lfg_fill(rng, dst, n, 1, (cudaStream_t)stream);
@@ -542,6 +548,7 @@ int rng_fill_uniform(gbrng_t rng, float* dst, int64_t n, void* stream)
 
 int rng_fill_normal(gbrng_t rng, float* dst, int64_t n, void* stream)
 {
+    NvtxRange range("rng_fill_normal");
     if (!rng || (n > 0 && !dst) || n < 0 || (n & 1))
         return fail(GBRNG_EINVAL, "bad fill arguments (n must be even)");
     if ((uintptr_t)dst & 7u) return fail(GBRNG_EINVAL, "normal fill needs an 8-byte aligned dst");
@@ -552,6 +559,7 @@ int rng_fill_normal(gbrng_t rng, float* dst, int64_t n, void* stream)
 
 int ld_init_equilibrium(ld_system* sys, void* stream)
 {
+    NvtxRange range("ld_init_equilibrium");
     GB_CHECK(check_system(sys, true));
     if (sys->n == 0) return GBRNG_OK;
     if (sys->rng->kind == GBRNG_LAGFIB) return lfg_ld(sys, 0, 1, nullptr, (cudaStream_t)stream);
@@ -560,6 +568,7 @@ int ld_init_equilibrium(ld_system* sys, void* stream)
 
 int ld_run(ld_system* sys, int64_t n_steps, ld_stats* out, void* stream)
 {
+    NvtxRange range("ld_run");
     GB_CHECK(check_system(sys, true));
     if (n_steps < 0) return fail(GBRNG_EINVAL, "n_steps must be >= 0");
     if (sys->rng->kind == GBRNG_LAGFIB) return lfg_ld(sys, n_steps, 0, out, (cudaStream_t)stream);
@@ -568,6 +577,7 @@ int ld_run(ld_system* sys, int64_t n_steps, ld_stats* out, void* stream)
 
 int ou_run(ou_system* sys, int64_t n_steps, int64_t every, double* mean, double* corr, void* stream)
 {
+    NvtxRange range("ou_run");
     if (!sys) return fail(GBRNG_EINVAL, "system is NULL");
     if (sys->n < 1 || !sys->R) return fail(GBRNG_EINVAL, "need n >= 1 and a device array R");
     if (n_steps < 0 || every < 1) return fail(GBRNG_EINVAL, "need n_steps >= 0 and every >= 1");
@@ -586,6 +596,7 @@ int ou_run(ou_system* sys, int64_t n_steps, int64_t every, double* mean, double*
 
 int ld_run_stepwise(ld_system* sys, int64_t n_steps, ld_stats* out, void* stream)
 {
+    NvtxRange range("ld_run_stepwise");
     GB_CHECK(check_system(sys, true));
     if (n_steps < 0) return fail(GBRNG_EINVAL, "n_steps must be >= 0");
     if (sys->rng->kind == GBRNG_LAGFIB)

@@ -279,3 +279,30 @@ def test_zero_steps_and_empty(G):
     G.ld_init_equilibrium(s2)
     st2 = G.ld_run(s2, 0)
     assert math.isclose(st2["sum_x2"], (s2.x.double() ** 2).sum().item(), rel_tol=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["taus", "ran2", "lagfib", "lcg"])
+def test_runs_are_bit_reproducible(G, kind):
+    """Two identical runs give identical trajectories, generator states and
+    statistics (fixed-order reductions, no atomics in any sum)."""
+    out = []
+    for _ in range(2):
+        r = G.rng_init(kind, 606, 3000)
+        x = torch.zeros((3000, 3), dtype=torch.float32, device="cuda")
+        s = G.LdSystem(r, x, torch.zeros_like(x))
+        G.ld_init_equilibrium(s)
+        st = G.ld_run(s, 250)
+        out.append((s.x.cpu().numpy().tobytes(), s.v.cpu().numpy().tobytes(),
+                    G.rng_get_state(r), st))
+    assert out[0][:3] == out[1][:3]
+    assert out[0][3] == out[1][3]
+
+
+def test_allocation_failure_reports_enomem(G):
+    """A generator larger than the device reports GBRNG_ENOMEM (no fault), and
+    the context stays usable."""
+    with pytest.raises(G.GbrngError) as e:
+        G.rng_init("taus", 1, 2 * 10**10)      # 320 GB of state, more than the device holds
+    assert e.value.code == -2
+    r = G.rng_init("taus", 1, 100)
+    assert G.rng_fill_u32(r, 1000).numel() == 1000
