@@ -39,11 +39,12 @@ struct Tile {
     int32_t pad;
 };
 
+// Hybrid Taus with one oscillator per thread gets a 51-register budget (five
+// 256-thread blocks per SM); the other shapes keep the compiler's choice.
 template <int KIND, int K>
-__global__ void __launch_bounds__(256, KIND == GBRNG_TAUS && K == 1 ? 5 : 1) batched_kernel(const SysDesc* __restrict__ sys,
-                                                      const Tile* __restrict__ tiles,
-                                                      int64_t n_tiles, int64_t n_steps,
-                                                      double* __restrict__ partials)
+__global__ void __launch_bounds__(256, KIND == GBRNG_TAUS && K == 1 ? 5 : 1)
+    batched_kernel(const SysDesc* __restrict__ sys, const Tile* __restrict__ tiles,
+                   int64_t n_tiles, int64_t n_steps, double* __restrict__ partials)
 {
     extern __shared__ int32_t tab[];   // Ran2: [K][32][T]
     __shared__ double red[4 * 32];

@@ -225,9 +225,8 @@ __device__ __forceinline__ void walk_blocks(const LfgArgs& a, int64_t q_first, i
 }
 
 // ------------------------------------------------------------- fused step
-// Box-Muller normals of one oscillator-step from its four values (Sec. III.A
-// of the Langevin model: gx, gy from the first pair, gz from the cosine branch
-// of the second).
+// Box-Muller normals of one oscillator-step from its four values (Sec. II.A;
+// gx, gy from the first pair, gz from the cosine branch of the second).
 __device__ __forceinline__ void normals3(uint4 w, float& g0, float& g1, float& g2)
 {
     box_muller_u32(w.x, w.y, g0, g1);
@@ -352,11 +351,11 @@ __global__ void __launch_bounds__(kLfgThreads, 3) lfg_kernel(LfgArgs a)
 // [c n_c, c n_c + n_c) for the whole launch and keeps their x and v in shared
 // memory: a step's global traffic is then the ring alone.  A round holds
 // floor(width / 4N) steps, since an oscillator's consecutive steps stay with
-// one lane and only the ring is shared.  A step's positions
-// for the CTA are one contiguous region; when none of its windows wraps around
-// the ring (all but about one step in R / 4N), each lane addresses the region
-// with one pointer per window and the blocks are walked two at a time, the
-// loads of one in flight while the other is consumed.
+// one lane and only the ring is shared.  A step's positions for the CTA are
+// one contiguous region; when none of its windows wraps around the ring (all
+// but about one step in R / 4N), each lane addresses the region with one
+// pointer per window and the blocks are walked two at a time, the loads of one
+// in flight while the other is consumed.
 constexpr int kResThreads = 512;
 constexpr int kResWarps = kResThreads / 32;
 
