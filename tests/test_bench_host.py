@@ -1,0 +1,53 @@
+"""Host-side arithmetic of bench.py (no GPU): the roofline fractions, the
+launch count claimed per timed step, the units of one step and the replica
+helpers."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+PEAKS = {"hbm_gbs": 6762.3, "sm_max_mhz": 2070.0}
+CLK = {"sm_mhz": 2070.0}
+
+
+def test_alu_roofline_uses_algorithmic_ops_and_measured_lanes():
+    units = bench.N_OSC * bench.LD_STEPS
+    r = bench.roofline("ld_taus", 61.7, units, PEAKS, "measured", CLK)
+    assert r["bound"] == "alu" and r["unit"] == "Tops/s"
+    assert r["achieved"] == pytest.approx(92 * units / 0.0617 / 1e12)
+    assert r["peak"] == pytest.approx(152 * 64 * 2070e6 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    adj = bench.roofline("adjoint_taus", 20.0, 10**9, PEAKS, "measured", CLK)
+    assert adj["achieved"] == pytest.approx(2 * 92 * 10**9 / 0.02 / 1e12)   # every draw twice
+
+
+def test_fill_and_lagfib_rooflines():
+    f = bench.roofline("fill_uniform_taus", 0.9, 0, PEAKS, "measured", CLK)
+    assert f["bound"] == "hbm" and f["achieved"] == pytest.approx(4 * 2**30 / 0.0009 / 1e9)
+    assert f["frac"] == pytest.approx(f["achieved"] / 6762.3)
+    l2 = bench.roofline("ld_lagfib", 117.0, 10**10, PEAKS, "measured", CLK, l2_gbs=7900.0)
+    assert l2["bound"] == "l2" and l2["achieved"] == pytest.approx(48 * 1e10 / 0.117 / 1e9)
+    assert bench.roofline("ld_lagfib", 117.0, 10**10, PEAKS, "m", CLK)["frac"] is None
+
+
+def test_launch_count_per_step():
+    parts = [(n, 0, None) for n in ("ld_taus", "ld_ran2", "ld_lagfib", "fill_uniform_taus",
+                                    "fill_normal_taus", "batched_taus", "adjoint_taus")]
+    # 3 fused x 2 + 2 fills + batched (1 launch + reduce) + adjoint x 2
+    assert bench.gpu_launches(parts, 1, (256, 1, 0)) == 6 + 2 + 2 + 2
+    # steps per launch L = 715 -> ceil(5000 / 715) = 7 launches + reduce
+    assert bench.gpu_launches(parts, 3, (128, 1, 715)) == 3 * (6 + 2 + 8 + 2)
+
+
+def test_step_units_and_replica_helpers():
+    u = bench._step_units()
+    assert u["ld_taus"] == 10**10 and u["fill_normal_lagfib"] == 2**30
+    assert u["adjoint_taus"] == 10**9
+    assert bench._step_osc_steps(u) == 3 * 10**10 + u["batched_taus"] + 10**9
+    assert bench.rank_seed(0) != bench.rank_seed(1)
+    assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
+    assert bench.whole_job_rate(4, 1e9, 500.0) == pytest.approx(8e9)
