@@ -8,7 +8,11 @@
  * thread (Sec. III.B, Algorithms 1-2), and the additive Lagged Fibonacci
  * generator shared by all threads (Sec. III.C, Algorithm 3, Table I) --
  * feeding Box-Muller normals (Sec. II.A) into the Langevin step of N
- * independent three-dimensional harmonic oscillators (Sec. I and IV).
+ * independent three-dimensional harmonic oscillators (Sec. I and IV).  Also:
+ * the Quick and Dirty LCG of Eq. 1 (Sec. II.B) as a fourth per-thread kind,
+ * the overdamped one-dimensional test of Sec. IV (Eq. 4-5), the paper's
+ * one-launch-per-step form of the fused step, a batched graph of many
+ * systems and a reverse-time adjoint.
  *
  * Conventions for every entry point:
  *  - The return value is a gbrng_status; nothing aborts.  On failure
@@ -26,6 +30,8 @@
  *  - Device errors map to GBRNG_ECUDA; a device-side wait that exceeded its
  *    limit (Lagged Fibonacci grid barrier) maps to GBRNG_ETIMEOUT, after which
  *    the handle's state is undefined (rng_set_state or a new handle recovers).
+ *  - Every call that launches work opens an NVTX range named after the call
+ *    (a no-op unless a profiler or tracer is attached).
  */
 #ifndef GBRNG_H
 #define GBRNG_H
