@@ -627,7 +627,7 @@ def run_reference(args, world):
 
 CASES = ("ld_taus", "ld_ran2", "ld_lagfib", "fill_uniform_taus", "fill_normal_taus",
          "fill_uniform_ran2", "fill_normal_ran2", "fill_uniform_lagfib", "fill_normal_lagfib",
-         "batched_taus")
+         "batched_taus", "adjoint_taus")
 
 
 def run_case(name: str):
@@ -637,7 +637,15 @@ def run_case(name: str):
     import torch
     from paper_1003_1123_gb300 import gbrng as G
     kind = name.split("_")[-1]
-    if name == "batched_taus":
+    if name == "adjoint_taus":
+        # the bench's adjoint system (1e5 oscillators), 1000 steps, checkpoints every 100
+        r = G.rng_init("taus", SEED + 11, ADJ_N)
+        x = torch.zeros((ADJ_N, 3), dtype=torch.float32, device="cuda")
+        s = G.LdSystem(r, x, torch.zeros_like(x), K_per=torch.ones(ADJ_N, device="cuda"), **PARAMS)
+        G.ld_init_equilibrium(s)
+        for _ in range(2):
+            G.ld_backward(s, 1000, ADJ_CKPT)
+    elif name == "batched_taus":
         # the bench's 512 systems; the second graph replay (autotuned shape
         # cached by the first) runs inside the NVTX range "profile"
         systems = []
