@@ -121,3 +121,14 @@ def test_ou_paper_curves_at_small_dt():
         t = r * every * dt
         sd = math.sqrt(kT / k_sp * (1 - math.exp(-2 * t / tau)) / n)
         assert abs(m - 10.0 * math.exp(-t / tau)) <= 4 * sd + 10.0 * 5e-4
+
+
+def test_lcg_first_outputs_from_zero():
+    """From x = 0 the first two words are c = 0x3C6EF35F and a c + c mod 2^32 =
+    0x47502932 (the Hybrid Taus LCG word advances the same way)."""
+    x = np.zeros(1, np.uint32)
+    assert oracle.lcg_next(x) == 0x3C6EF35F
+    assert oracle.lcg_next(x) == 0x47502932
+    y = np.array([0, 0, 0, 0], np.uint32)
+    oracle.taus_next(y)
+    assert int(y[3]) == 0x3C6EF35F
