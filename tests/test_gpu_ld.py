@@ -182,12 +182,36 @@ def test_lagfib_large_n_parity(G):
     assert G.parse_state(G.rng_get_state(s.rng))[1] == oracle_state_bytes(g)
 
 
+def test_lagfib_streamed_rounds_large_n(G):
+    """N = 2.5e6 on the last Table I row (4N = 2.5 rounds a step, rounds
+    straddling step boundaries, two rounds within N oscillator-steps so the
+    x, v copies for the next round are issued before the barrier), per-
+    oscillator K: full trajectories and generator state vs the oracle."""
+    n = 2_500_001
+    Kper = W.spring_constants(n, 9)
+    r = G.rng_init("lagfib", 515, n)
+    x = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+    s = G.LdSystem(r, x, torch.zeros_like(x), K_per=torch.from_numpy(Kper).cuda())
+    g = oracle.Gen("lagfib", 515, n)
+    p = oracle.params()
+    G.ld_init_equilibrium(s)
+    xo, vo = oracle.ld_init_eq_f32(g, n, p, Kper=Kper)
+    for steps in (1, 3):
+        st = G.ld_run(s, steps)
+        ost = oracle.ld_run_f32(g, xo, vo, p, steps, Kper=Kper)
+        assert rel_err(s.x.cpu().numpy(), xo) < TRAJ_TOL and rel_err(s.v.cpu().numpy(), vo) < TRAJ_TOL
+        assert math.isclose(st["energy_time_avg"], ost["energy_time_avg"], rel_tol=1e-5)
+    assert G.parse_state(G.rng_get_state(s.rng))[1] == oracle_state_bytes(g)
+
+
 @pytest.mark.parametrize("row,n,init", [
     (0, 200, True),      # 4N <= D: one round per step from position 0 on
     (3, 4096, True),     # D < 4N <= 2D, after the first ll positions: one round per step
     (3, 4096, False),    # same, but the run starts below ll with 4N > D
     (0, 1000, True),     # 4N > 2D: several rounds per step
     (2, 3001, True),     # ragged N, 4N between D and 2D
+    (0, 4099, True),     # ~8 rounds a step: x, v copies for the next round cross the barrier
+    (1, 2000, False),    # ~3 rounds a step from position 0, copies cross the barrier
 ])
 def test_lagfib_rows_and_round_shapes(G, row, n, init):
     """The shared Lagged Fibonacci sequence drives the fused step for every
