@@ -28,7 +28,12 @@ def test_alu_roofline_uses_algorithmic_ops_and_measured_lanes():
 def test_fill_and_lagfib_rooflines():
     f = bench.roofline("fill_uniform_taus", 0.9, 0, PEAKS, "measured", CLK)
     assert f["bound"] == "hbm" and f["achieved"] == pytest.approx(4 * 2**30 / 0.0009 / 1e9)
-    assert f["frac"] == pytest.approx(f["achieved"] / 6762.3)
+    assert f["frac"] == pytest.approx(f["achieved"] / 6762.3) and "alt" not in f
+    lf = bench.roofline("fill_uniform_lagfib", 2.4, 0, PEAKS, "measured", CLK, l2_gbs=7900.0)
+    assert lf["bound"] == "l2" and lf["achieved"] == pytest.approx(16 * 2**30 / 0.0024 / 1e9)
+    assert lf["frac"] == pytest.approx(lf["achieved"] / 7900.0)
+    assert lf["alt"]["bound"] == "hbm"
+    assert lf["alt"]["achieved"] == pytest.approx(4 * 2**30 / 0.0024 / 1e9)
     l2 = bench.roofline("ld_lagfib", 117.0, 10**10, PEAKS, "measured", CLK, l2_gbs=7900.0)
     assert l2["bound"] == "l2" and l2["achieved"] == pytest.approx(48 * 1e10 / 0.117 / 1e9)
     assert bench.roofline("ld_lagfib", 117.0, 10**10, PEAKS, "m", CLK)["frac"] is None
