@@ -178,16 +178,23 @@ class Workload:
         self.fill_rngs = {k: G.rng_init(k, seed + 7, N_OSC) for k in KINDS}
         self.out = torch.empty(FILL_N, dtype=torch.float32, device="cuda")
         self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-        # batched: 512 uneven systems (Hybrid Taus), one graph launch per call
+        # batched: 512 uneven systems (Hybrid Taus), one graph launch per call;
+        # their x, v are consecutive slices of two arrays, so a host round trip
+        # of the whole batch is one copy each way
+        specs = W.batched_systems(BATCH_SYSTEMS, seed=1234 + rank)
+        self.batch_osc = sum(sp["n"] for sp in specs)
+        self.batch_x = torch.zeros((self.batch_osc, 3), dtype=torch.float32, device="cuda")
+        self.batch_v = torch.zeros_like(self.batch_x)
         self.batch = []
-        for i, sp in enumerate(W.batched_systems(BATCH_SYSTEMS, seed=1234 + rank)):
+        off = 0
+        for sp in specs:
             r = G.rng_init("taus", sp["seed"], sp["n"])
-            x = torch.zeros((sp["n"], 3), dtype=torch.float32, device="cuda")
-            s = G.LdSystem(r, x, torch.zeros_like(x), K=sp["K"], m=sp["m"], gamma=sp["gamma"],
-                           kT=sp["kT"], dt=sp["dt"])
+            n = sp["n"]
+            s = G.LdSystem(r, self.batch_x[off:off + n], self.batch_v[off:off + n], K=sp["K"],
+                           m=sp["m"], gamma=sp["gamma"], kT=sp["kT"], dt=sp["dt"])
             G.ld_init_equilibrium(s)
             self.batch.append(s)
-        self.batch_osc = sum(s.n for s in self.batch)
+            off += n
         # adjoint: 1e5 oscillators, K per oscillator, checkpoints every 100 steps
         ra = G.rng_init("taus", seed + 11, ADJ_N)
         xa = torch.zeros((ADJ_N, 3), dtype=torch.float32, device="cuda")
@@ -376,7 +383,7 @@ def run_e2e(args, wl, parts, G, torch):
     host = {}
     for kind, s in wl.systems.items():
         host[kind] = (s.x.cpu().pin_memory(), s.v.cpu().pin_memory())
-    host_batch = [(s.x.cpu().pin_memory(), s.v.cpu().pin_memory()) for s in wl.batch]
+    host_batch = (wl.batch_x.cpu().pin_memory(), wl.batch_v.cpu().pin_memory())
     host_adj = (wl.adj.x.cpu().pin_memory(), wl.adj.v.cpu().pin_memory(),
                 torch.empty(ADJ_N, dtype=torch.float32).pin_memory())
     probe = torch.empty(1024, dtype=torch.float32).pin_memory()
@@ -387,15 +394,14 @@ def run_e2e(args, wl, parts, G, torch):
         h2d = d2h = 0
         for name, _, fn in parts:
             if name.startswith("batched"):
-                for s, (hx, hv) in zip(wl.batch, host_batch):
-                    s.x.copy_(hx, non_blocking=True)
-                    s.v.copy_(hv, non_blocking=True)
-                    h2d += 2 * hx.numel() * 4
+                hx, hv = host_batch
+                wl.batch_x.copy_(hx, non_blocking=True)
+                wl.batch_v.copy_(hv, non_blocking=True)
+                h2d += 2 * hx.numel() * 4
                 fn()
-                for s, (hx, hv) in zip(wl.batch, host_batch):
-                    hx.copy_(s.x, non_blocking=True)
-                    hv.copy_(s.v, non_blocking=True)
-                    d2h += 2 * hx.numel() * 4 + 40
+                hx.copy_(wl.batch_x, non_blocking=True)
+                hv.copy_(wl.batch_v, non_blocking=True)
+                d2h += 2 * hx.numel() * 4 + 40 * len(wl.batch)
             elif name.startswith("adjoint"):
                 hx, hv, hd = host_adj
                 wl.adj.x.copy_(hx, non_blocking=True)
