@@ -129,6 +129,32 @@ def test_zero_noise_closed_form(G, kind):
     assert np.abs(s.v.cpu().numpy() - ve).max() < 5e-6 * scale
 
 
+@pytest.mark.parametrize("kind", KINDS + ["lcg"])
+def test_zero_friction_is_noise_free(G, kind):
+    """gamma = 0, a degenerate case of the Langevin equation (Sec. I): the
+    random force's amplitude sqrt(2 gamma kT dt) is zero, so the trajectory is
+    the deterministic Euler map whatever the draws -- bit-identical to the
+    binary32 oracle and within binary32 rounding of A^n s0 (FP64) -- while
+    the generator still advances by four draws a step."""
+    n, steps = 1500, 600
+    K, m, dt = 0.7, 1.3, 0.02
+    s, g, p = make_pair(G, kind, n, 4, K=K, m=m, gamma=0.0, kT=2.0, dt=dt)
+    x0, v0 = W.initial_state(n, 5)
+    s.x.copy_(torch.from_numpy(x0))
+    s.v.copy_(torch.from_numpy(v0))
+    G.ld_run(s, steps, stats=False)
+    xo, vo = x0.copy(), v0.copy()
+    oracle.ld_run_f32(g, xo, vo, p, steps)
+    assert np.array_equal(s.x.cpu().numpy(), xo) and np.array_equal(s.v.cpu().numpy(), vo)
+    assert G.parse_state(G.rng_get_state(s.rng))[1] == oracle_state_bytes(g)
+    A = np.array([[1.0, dt], [-dt * K / m, 1.0]])
+    An = np.linalg.matrix_power(A, steps)
+    xe = An[0, 0] * x0.astype(np.float64) + An[0, 1] * v0
+    ve = An[1, 0] * x0.astype(np.float64) + An[1, 1] * v0
+    scale = max(np.abs(xe).max(), np.abs(ve).max())
+    assert np.abs(xo - xe).max() < 5e-6 * scale and np.abs(vo - ve).max() < 5e-6 * scale
+
+
 @pytest.mark.parametrize("kind", KINDS)
 def test_equipartition_large(G, kind):
     """N = 10^6 from the equilibrium draw, 2000 steps: <x^2>, <v^2> match the

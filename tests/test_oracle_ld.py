@@ -37,6 +37,32 @@ def test_zero_noise_matches_matrix_power(kind):
     assert np.abs(xf - xe).max() < 5e-6 * scale and np.abs(vf - ve).max() < 5e-6 * scale
 
 
+@pytest.mark.parametrize("kind", ["taus", "ran2", "lagfib", "lcg"])
+def test_zero_friction_removes_the_noise(kind):
+    """gamma = 0 with kT > 0: the random force's amplitude sqrt(2 kT gamma dt)
+    (Sec. I) vanishes with the friction, so the FP64 run is the undamped map
+    A^n s_0 although kT > 0 (a noise amplitude missing its gamma would fail),
+    and the generator still advances by four draws a particle-step."""
+    n, steps = 48, 400
+    K, m, dt = 0.9, 1.2, 0.02
+    p = oracle.params(K=K, m=m, gamma=0.0, kT=3.0, dt=dt)
+    rng = np.random.default_rng(3)
+    x0 = rng.standard_normal((n, 3))
+    v0 = rng.standard_normal((n, 3))
+    x, v = x0.copy(), v0.copy()
+    g = oracle.Gen(kind, 9, n)
+    oracle.ld_run_f64(g, x, v, p, steps)
+    An = np.linalg.matrix_power(_A(K, m, 0.0, dt), steps)
+    assert np.allclose(x, An[0, 0] * x0 + An[0, 1] * v0, rtol=1e-11, atol=1e-12)
+    assert np.allclose(v, An[1, 0] * x0 + An[1, 1] * v0, rtol=1e-11, atol=1e-12)
+    ref = oracle.Gen(kind, 9, n)
+    ref.fill_u32(4 * n * steps)
+    if kind == "lagfib":
+        assert np.array_equal(g.ring_in_order(), ref.ring_in_order())
+    else:
+        assert np.array_equal(g.state, ref.state)
+
+
 def test_zero_noise_first_order_convergence():
     """The scheme is first order in dt: against the exact underdamped
     oscillator x(t) = e^{-gt/2m}(x0 cos wt + ((v0 + g x0/2m)/w) sin wt), the
