@@ -25,12 +25,12 @@ struct LdArgs {
     double* partials;  // [gridDim.x][4]
 };
 
-// Register budget: 48 per thread for Hybrid Taus and the LCG (ten 128-thread
-// blocks per SM; measured faster than 64 registers and eight blocks); for Ran2
-// six blocks per SM (up to 85 registers, no spills), measured 5% faster than
-// nine blocks at 56 registers and than seven or eight blocks.
+// Register budget (128-thread blocks per SM, measured at 1e6 oscillators):
+// Hybrid Taus and Ran2 six (up to 85 registers, no spills; Taus 1% and Ran2 5%
+// faster than ten and nine blocks at 48 and 56 registers, which spilled), the
+// LCG seven (5% faster than ten).
 template <int KIND, bool INIT>
-__global__ void __launch_bounds__(128, KIND == GBRNG_RAN2 ? 6 : 10) ld_pt_kernel(LdArgs a)
+__global__ void __launch_bounds__(128, KIND == GBRNG_LCG ? 7 : 6) ld_pt_kernel(LdArgs a)
 {
     extern __shared__ int32_t tab[];   // Ran2: [32][blockDim.x]
     __shared__ double red[4 * 32];
