@@ -36,7 +36,8 @@ namespace gb {
 
 enum { LFG_U32 = 0, LFG_UNIFORM = 1, LFG_NORMAL = 2, LFG_LD = 3, LFG_LD_INIT = 4 };
 
-constexpr int kLfgThreads = 256;   // three CTAs per SM (80 registers): 24 warps to hide HBM latency
+constexpr int kLfgThreads = 256;   // three CTAs per SM (80 registers): 24 warps to hide HBM latency;
+                                   // two or four CTAs per SM: fills 5-6% slower
 constexpr int kLfgWarps = kLfgThreads / 32;
 constexpr int kLfgDepth = 2;     // blocks per warp with lag loads in flight
 
