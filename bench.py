@@ -453,7 +453,7 @@ def roofline(part, ms, units, peaks, src, clk, l2_gbs=None):
     """Roofline of one part against its binding resource.  Taus/Ran2 fused,
     batched and adjoint work: the INT32 lanes (algorithmic integer ops of the
     generator: 92 or 88 per oscillator-step; the adjoint draws every number
-    twice).  Lagged Fibonacci fused steps: the L2 copy bandwidth measured in
+    once when it keeps the run's noise, as it does at this size).  Lagged Fibonacci fused steps: the L2 copy bandwidth measured in
     this run (48 algorithmic bytes per oscillator-step).  Taus/Ran2 fills: the
     HBM copy bandwidth (4 B per number).  Lagged Fibonacci fills: L2 (16 B per
     number), with the HBM figure beside it as `alt`."""
@@ -479,8 +479,7 @@ def roofline(part, ms, units, peaks, src, clk, l2_gbs=None):
                 "unit": "GB/s", "frac": achieved / l2_gbs if l2_gbs else None, "traffic": None,
                 "peak_source": "L2-resident copy of 2 x 32 MiB measured in this run; "
                                "algorithmic 48 B per oscillator-step"}
-    draws = 2 if part.startswith("adjoint") else 1
-    ops = draws * INT_OPS_PER_OSC_STEP[kind] * units
+    ops = INT_OPS_PER_OSC_STEP[kind] * units
     achieved = ops / sec / 1e12
     peak = SMS * INT32_LANES_PER_SM * mhz * 1e6 / 1e12
     return {"kernel": part, "bound": "alu", "achieved": achieved, "peak": peak,

@@ -266,15 +266,28 @@ int ld_batched_tune(const ld_system* sys, int n_sys, int* tune_out);
 
 /* Reverse-time adjoint of L = (1/S) sum_{t=1..S} E(t) (S = n_steps) under the
  * fixed noise of the generator, starting from the system's current state.
- * Generator states and (x, v) are checkpointed every ckpt_every steps; the
- * noise of each segment is regenerated bit-exactly for its reverse sweep.
+ * Generator states and (x, v) are checkpointed every ckpt_every steps.  The
+ * reverse sweep reads the noise the forward run stored (12 B per
+ * oscillator-step) when that history fits the limit of
+ * ld_set_adjoint_history_limit, and otherwise regenerates each segment's noise
+ * bit-exactly from its checkpoint; the results are identical.  The scratch
+ * (checkpoints, noise) stays with the handle for later calls until
+ * rng_destroy.
  * Leaves the system advanced exactly as ld_run(sys, n_steps) would.
  * dK_per (device [n], nullable) receives dL/dK_i; *dgamma, *dkT (nullable)
  * receive dL/dgamma, dL/dkT; *loss (nullable) receives L.  Per-thread kinds
  * only; requires gamma > 0, kT > 0, n_steps >= 1, ckpt_every >= 1.
- * Synchronises stream. */
+ * GBRNG_ENOMEM if the scratch cannot be allocated.  Synchronises stream. */
 int ld_backward(ld_system* sys, int64_t n_steps, int ckpt_every, float* dK_per,
                 double* dgamma, double* dkT, double* loss, void* stream);
+
+/* The largest noise history (bytes) ld_backward keeps instead of regenerating
+ * the noise segment by segment: 0 always regenerates; -1 (the default) allows
+ * half the device memory free at the call (counting the handle's own adjoint
+ * scratch as free).  Process-wide; GBRNG_EINVAL for
+ * values below -1.  (The paper has no adjoint; this trades memory for the
+ * second generator pass of the reverse sweep.) */
+int ld_set_adjoint_history_limit(int64_t bytes);
 
 /* ld_run for callers that cannot allocate device memory when they step a
  * system: work recorded under CUDA stream capture (cudaMalloc is not a stream

@@ -6,9 +6,11 @@
 //  A) the forward run, writing a checkpoint (x, v, generator state) at the
 //     start of every segment of P steps, accumulating L and the direct part
 //     of dL/dK_i, and finally the end state;
-//  B) the reverse sweep, segment by segment from the last: the generator is
-//     restored from the segment's checkpoint and the segment's normals are
-//     regenerated bit-exactly into a scratch buffer (3 floats per step); then,
+//  B) the reverse sweep, segment by segment from the last: the segment's
+//     normals (3 floats per step) are either read from the history A wrote
+//     when the whole run's noise fits the history limit, or regenerated
+//     bit-exactly into a scratch buffer from the segment's checkpointed
+//     generator state; then,
 //     walking the segment backwards from its exact end state (the next
 //     checkpoint, or the final state), each step is inverted,
 //        v_t = (v_{t+1} + b x_{t+1} - c g_t) / (a + b dt),  x_t = x_{t+1} - dt v_t,
@@ -23,6 +25,7 @@
 // state), where it is stable.  Sums over steps are Kahan-compensated binary32,
 // sums over oscillators fixed-order doubles.
 #include <algorithm>
+#include <atomic>
 
 #include "device.cuh"
 #include "internal.cuh"
@@ -40,7 +43,8 @@ struct AdjArgs {
     int32_t* r2;
     int64_t streams;
     float* ckpt;        // [nseg][6 + state words][n]
-    float* gbuf;        // [P][3][n]
+    float* gbuf;        // [S][3][n] history (hist) or [P][3][n] segment scratch
+    int hist;
     float* dK;          // [n] or null
     double* partials;   // [grid][4]: loss, dgamma, dkT, unused
 };
@@ -131,6 +135,10 @@ __global__ void __launch_bounds__(64, 12) adjoint_kernel(AdjArgs a)
             for (int64_t t = 0; t < len; ++t) {
                 float g[3];
                 if (KIND == GBRNG_TAUS) td.normals3(g[0], g[1], g[2]); else rd.normals3(g[0], g[1], g[2]);
+                if (a.hist) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) a.gbuf[((seg * a.P + t) * 3 + q) * n + i] = g[q];
+                }
 #pragma unroll
                 for (int q = 0; q < 3; ++q) em_component(c.cdt, c.cva, ckx, c.cs, g[q], x[q], v[q]);
                 loss.add(energy3(hK, c.hm, x[0], x[1], x[2], v[0], v[1], v[2]));
@@ -163,13 +171,16 @@ __global__ void __launch_bounds__(64, 12) adjoint_kernel(AdjArgs a)
         for (int64_t seg = a.nseg - 1; seg >= 0; --seg) {
             const float* ck = a.ckpt + seg * CW * n + i;
             const int64_t len = min(a.P, a.S - seg * a.P);
-            load_state(ck + 6 * n, n);
-            for (int64_t t = 0; t < len; ++t) {
-                float g[3];
-                if (KIND == GBRNG_TAUS) td.normals3(g[0], g[1], g[2]); else rd.normals3(g[0], g[1], g[2]);
+            if (!a.hist) {
+                load_state(ck + 6 * n, n);
+                for (int64_t t = 0; t < len; ++t) {
+                    float g[3];
+                    if (KIND == GBRNG_TAUS) td.normals3(g[0], g[1], g[2]); else rd.normals3(g[0], g[1], g[2]);
 #pragma unroll
-                for (int q = 0; q < 3; ++q) a.gbuf[(t * 3 + q) * n + i] = g[q];
+                    for (int q = 0; q < 3; ++q) a.gbuf[(t * 3 + q) * n + i] = g[q];
+                }
             }
+            const float* gseg = a.gbuf + (a.hist ? seg * a.P * 3 * n : 0);
             float xn[3] = {xe[0], xe[1], xe[2]}, vn[3] = {ve[0], ve[1], ve[2]};
             for (int64_t t = len - 1; t >= 0; --t) {
                 const int64_t tg = seg * a.P + t;   // global step index
@@ -177,7 +188,7 @@ __global__ void __launch_bounds__(64, 12) adjoint_kernel(AdjArgs a)
                 float ddk = 0.f, ddg = 0.f, ddT = 0.f;
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    gk[q] = a.gbuf[(t * 3 + q) * n + i];
+                    gk[q] = gseg[(t * 3 + q) * n + i];
                     vt[q] = (vn[q] + ckx * xn[q] - c.cs * gk[q]) * inv_ab;
                     xt[q] = xn[q] - c.cdt * vt[q];
                 }
@@ -225,14 +236,20 @@ __global__ void __launch_bounds__(64, 12) adjoint_kernel(AdjArgs a)
         for (int k = 0; k < 4; ++k) a.partials[4 * blockIdx.x + k] = acc[k];
 }
 
-struct AdjScratch {
-    float* buf = nullptr;
-    size_t bytes = 0;
-};
+// Largest noise history (bytes) ld_backward keeps; -1: half the free device
+// memory at the call.
+std::atomic<int64_t> g_hist_limit{-1};
 
 }  // namespace gb
 
 using namespace gb;
+
+extern "C" int ld_set_adjoint_history_limit(int64_t bytes)
+{
+    if (bytes < -1) return fail(GBRNG_EINVAL, "history limit must be >= -1, got %lld", (long long)bytes);
+    g_hist_limit.store(bytes);
+    return GBRNG_OK;
+}
 
 extern "C" int ld_backward(ld_system* sys, int64_t n_steps, int ckpt_every, float* dK_per,
                            double* dgamma, double* dkT, double* loss, void* stream)
@@ -256,12 +273,23 @@ extern "C" int ld_backward(ld_system* sys, int64_t n_steps, int ckpt_every, floa
     const int64_t nseg = (n_steps + P - 1) / P;
     const int SW = h->kind == GBRNG_TAUS ? 4 : 35;
     const size_t ck_bytes = sizeof(float) * (size_t)nseg * (6 + SW) * (size_t)n;
-    const size_t g_bytes = sizeof(float) * (size_t)P * 3 * (size_t)n;
-    float* scratch = nullptr;
-    if (cudaMallocAsync((void**)&scratch, ck_bytes + g_bytes, st) != cudaSuccess) {
+    // the whole run's noise (12 B per oscillator-step) when it fits the limit,
+    // else one segment's
+    // (the scratch stays with the handle for the next call; the automatic
+    // limit counts what the handle already holds as free)
+    const size_t hist_bytes = sizeof(float) * 3 * (size_t)n_steps * (size_t)n;
+    const size_t seg_bytes = sizeof(float) * (size_t)P * 3 * (size_t)n;
+    int64_t limit = g_hist_limit.load();
+    if (limit < 0) {
+        size_t free_b = 0, total_b = 0;
+        limit = cudaMemGetInfo(&free_b, &total_b) == cudaSuccess
+                    ? (int64_t)((free_b + h->adj_bytes) / 2) : 0;
         cudaGetLastError();
-        return fail(GBRNG_ENOMEM, "adjoint scratch of %zu bytes", ck_bytes + g_bytes);
     }
+    bool hist = n_steps > P && (int64_t)hist_bytes <= limit;
+    if (hist && ensure_adj(h, ck_bytes + hist_bytes) != GBRNG_OK) hist = false;
+    if (!hist) GB_CHECK(ensure_adj(h, ck_bytes + seg_bytes));
+    float* scratch = h->adj;
     DevInfo di;
     GB_CHECK(dev_info(h->device, &di));
     const int T = 64;
@@ -273,11 +301,7 @@ extern "C" int ld_backward(ld_system* sys, int64_t n_steps, int ckpt_every, floa
     if (e != cudaSuccess || occ < 1) occ = 1;
     // one full resident wave at most; oscillators i, i + W, ... per thread
     const int64_t blocks = std::min<int64_t>((int64_t)di.sms * occ, (n + T - 1) / T);
-    int rc = ensure_partials(h, blocks);
-    if (rc != GBRNG_OK) {
-        cudaFreeAsync(scratch, st);
-        return rc;
-    }
+    GB_CHECK(ensure_partials(h, blocks));
     AdjArgs a;
     a.n = n;
     a.S = n_steps;
@@ -297,6 +321,7 @@ extern "C" int ld_backward(ld_system* sys, int64_t n_steps, int ckpt_every, floa
     a.streams = h->n;
     a.ckpt = scratch;
     a.gbuf = scratch + ck_bytes / sizeof(float);
+    a.hist = hist ? 1 : 0;
     a.dK = dK_per;
     a.partials = h->partials;
     if (h->kind == GBRNG_TAUS)
@@ -304,7 +329,6 @@ extern "C" int ld_backward(ld_system* sys, int64_t n_steps, int ckpt_every, floa
     else
         adjoint_kernel<GBRNG_RAN2><<<(unsigned)blocks, T, smem, st>>>(a);
     e = cudaGetLastError();
-    cudaFreeAsync(scratch, st);
     if (e != cudaSuccess) return fail(GBRNG_ECUDA, "adjoint launch failed: %s", cudaGetErrorString(e));
     ld_stats tmp;
     GB_CHECK(finish_stats(h, blocks, 1, &tmp, st));

@@ -70,6 +70,8 @@ struct Handle {
     double* dstats = nullptr;       // 8 doubles of final statistics
     float2* eacc = nullptr;         // paper-form runs: per-oscillator energy sum (Kahan s, c)
     int64_t eacc_cap = 0;
+    float* adj = nullptr;           // adjoint checkpoints and noise (history or one segment)
+    size_t adj_bytes = 0;
 };
 
 // Device attributes used for launch sizing (cached per device).
@@ -110,6 +112,7 @@ int lfg_ld(const ld_system* s, int64_t n_steps, int init, ld_stats* out, cudaStr
 int ld_run_stepwise_pt(const ld_system* s, int64_t n_steps, ld_stats* out, cudaStream_t st);
 int lfg_ld_stepwise(const ld_system* s, int64_t n_steps, ld_stats* out, cudaStream_t st);
 int ensure_eacc(Handle* h, int64_t n);
+int ensure_adj(Handle* h, size_t bytes);
 // Final-state sums and the per-oscillator energy sums of a paper-form run.
 int stepwise_stats(Handle* h, const ld_system* s, int64_t n_steps, ld_stats* out, cudaStream_t st);
 

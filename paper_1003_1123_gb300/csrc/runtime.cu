@@ -80,6 +80,20 @@ int ensure_eacc(Handle* h, int64_t n)
     return GBRNG_OK;
 }
 
+int ensure_adj(Handle* h, size_t bytes)
+{
+    if (bytes <= h->adj_bytes) return GBRNG_OK;
+    if (h->adj) cudaFree(h->adj);
+    h->adj = nullptr;
+    h->adj_bytes = 0;
+    if (cudaMalloc((void**)&h->adj, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(GBRNG_ENOMEM, "adjoint scratch of %zu bytes", bytes);
+    }
+    h->adj_bytes = bytes;
+    return GBRNG_OK;
+}
+
 int ensure_progress(Handle* h, int64_t count)
 {
     if (count <= h->progress_cap) return GBRNG_OK;
@@ -184,6 +198,7 @@ static void free_handle(Handle* h)
     cudaFree(h->partials);
     cudaFree(h->dstats);
     cudaFree(h->eacc);
+    cudaFree(h->adj);
     delete static_cast<gbrng_rng*>(h);
 }
 

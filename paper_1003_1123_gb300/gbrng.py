@@ -86,6 +86,7 @@ SIGNATURES = {
                               C.POINTER(C.c_double), C.c_void_p]),
     "ld_run_noalloc": (C.c_int, [C.POINTER(LdSystemC), C.c_int64, C.POINTER(LdStatsC),
                                  C.c_void_p]),
+    "ld_set_adjoint_history_limit": (C.c_int, [C.c_int64]),
     "gbrng_last_error": (C.c_char_p, []),
 }
 
@@ -238,6 +239,12 @@ def rng_set_state(rng: Rng, blob: bytes):
 
 def rng_set_wait_limit_ns(ns: int):
     _check(lib().rng_set_wait_limit_ns(ns))
+
+
+def ld_set_adjoint_history_limit(nbytes: int):
+    """Largest noise history ld_backward keeps (bytes; 0 always regenerates,
+    -1 half the free device memory)."""
+    _check(lib().ld_set_adjoint_history_limit(nbytes))
 
 
 def gbrng_test_stall_chunk(chunk: int):

@@ -22,7 +22,7 @@ def test_alu_roofline_uses_algorithmic_ops_and_measured_lanes():
     assert r["peak"] == pytest.approx(152 * 64 * 2070e6 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     adj = bench.roofline("adjoint_taus", 20.0, 10**9, PEAKS, "measured", CLK)
-    assert adj["achieved"] == pytest.approx(2 * 92 * 10**9 / 0.02 / 1e12)   # every draw twice
+    assert adj["achieved"] == pytest.approx(92 * 10**9 / 0.02 / 1e12)   # every number drawn once
 
 
 def test_fill_and_lagfib_rooflines():

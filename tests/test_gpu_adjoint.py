@@ -131,3 +131,32 @@ def test_autograd_function(G):
     assert torch.allclose(K.grad, 2 * ref["dK"], rtol=1e-6, atol=0)
     assert math.isclose(gamma.grad.item(), 2 * ref["dgamma"], rel_tol=1e-9)
     assert math.isclose(kT.grad.item(), 2 * ref["dkT"], rel_tol=1e-9)
+
+
+@pytest.mark.parametrize("kind", ["taus", "ran2"])
+@pytest.mark.parametrize("steps,ckpt", [(2000, 100), (1037, 64), (301, 7)])
+def test_noise_history_equals_regeneration(G, kind, steps, ckpt):
+    """The reverse sweep reading the noise stored by the forward run and the
+    one regenerating it segment by segment give identical gradients, loss,
+    final state and generator state, bit for bit."""
+    n = 777
+    Kper = W.spring_constants(n, 5, 0.5, 2.0)
+    x0, v0 = W.initial_state(n, 19)
+    out = []
+    try:
+        for limit in (0, 1 << 40):
+            G.ld_set_adjoint_history_limit(limit)
+            s = make(G, kind, n, 91, Kper, gamma=0.7, kT=1.3, start=(x0, v0))
+            r = G.ld_backward(s, steps, ckpt)
+            out.append((r["dK"].cpu().numpy().tobytes(), r["loss"], r["dgamma"], r["dkT"],
+                        s.x.cpu().numpy().tobytes(), s.v.cpu().numpy().tobytes(),
+                        G.rng_get_state(s.rng)))
+    finally:
+        G.ld_set_adjoint_history_limit(-1)
+    assert out[0] == out[1]
+
+
+def test_history_limit_rejects_bad_values(G):
+    with pytest.raises(G.GbrngError):
+        G.ld_set_adjoint_history_limit(-2)
+    G.ld_set_adjoint_history_limit(-1)
