@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(64, 12) adjoint_kernel(AdjArgs a)
 
 // Largest noise history (bytes) ld_backward keeps; -1: half the free device
 // memory at the call.
-std::atomic<int64_t> g_hist_limit{-1};
+static std::atomic<int64_t> g_hist_limit{-1};
 
 }  // namespace gb
 

@@ -614,7 +614,8 @@ static int launch_common(Handle* h, LfgArgs& a, int64_t G, cudaStream_t st)
     a.arrive = h->progress;
     a.status = h->dstatus;
     a.wait_ns = wait_limit_ns();
-    a.stall_cta = test_stall_chunk() < 0 ? -1 : (int)(test_stall_chunk() % G);
+    const int64_t stall = test_stall_chunk();
+    a.stall_cta = stall < 0 ? -1 : (int)(stall % G);
     GB_CUDA(cudaMemsetAsync(h->progress, 0, sizeof(uint64_t), st));
     GB_CUDA(cudaMemsetAsync(h->dstatus, 0, sizeof(int), st));
     return GBRNG_OK;

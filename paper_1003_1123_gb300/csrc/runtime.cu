@@ -1,4 +1,5 @@
 // Handles, errors, seeding kernels, state blobs and statistics finishing.
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -46,11 +47,12 @@ int dev_info(int device, DevInfo* out)
     return GBRNG_OK;
 }
 
-static uint64_t g_wait_ns = 2000000000ull;
-uint64_t wait_limit_ns() { return g_wait_ns; }
+// Process-wide settings (set from any host thread, read at each launch).
+static std::atomic<uint64_t> g_wait_ns{2000000000ull};
+uint64_t wait_limit_ns() { return g_wait_ns.load(); }
 
-static int64_t g_stall_chunk = -1;
-int64_t test_stall_chunk() { return g_stall_chunk; }
+static std::atomic<int64_t> g_stall_chunk{-1};
+int64_t test_stall_chunk() { return g_stall_chunk.load(); }
 
 int ensure_partials(Handle* h, int64_t count)
 {
@@ -345,14 +347,14 @@ const char* gbrng_last_error(void) { return g_msg; }
 int rng_set_wait_limit_ns(uint64_t ns)
 {
     if (ns == 0) return fail(GBRNG_EINVAL, "wait limit must be > 0");
-    g_wait_ns = ns;
+    g_wait_ns.store(ns);
     return GBRNG_OK;
 }
 
 int gbrng_test_stall_chunk(int64_t chunk)
 {
     if (chunk < -1) return fail(GBRNG_EINVAL, "chunk must be >= -1");
-    g_stall_chunk = chunk;
+    g_stall_chunk.store(chunk);
     return GBRNG_OK;
 }
 
