@@ -86,6 +86,9 @@ __global__ void __launch_bounds__(256, KIND == GBRNG_TAUS && K == 1 ? 6 : 1)
         }
         for (int64_t t0 = 0; t0 < n_steps; t0 += kEnergyBlock) {
             const int nb = (int)min((int64_t)kEnergyBlock, n_steps - t0);
+            // two oscillators a thread: two steps a loop iteration (4% faster
+            // on 512 uneven systems; one oscillator a thread is slower unrolled)
+#pragma unroll(K == 2 ? 2 : 1)
             for (int k = 0; k < nb; ++k) {
 #pragma unroll
                 for (int j = 0; j < K; ++j) {

@@ -76,6 +76,9 @@ __global__ void __launch_bounds__(128, KIND == GBRNG_LCG ? 7 : 6) ld_pt_kernel(L
             hK = 0.5f * Ki;
             for (int64_t t0 = 0; t0 < a.n_steps; t0 += kEnergyBlock) {
                 const int nb = (int)min((int64_t)kEnergyBlock, a.n_steps - t0);
+                // the LCG draws cheaply enough to gain from two steps a loop
+                // iteration (3% faster); Taus and Ran2 lose 1-2%
+#pragma unroll(KIND == GBRNG_LCG ? 2 : 1)
                 for (int k = 0; k < nb; ++k) {
                     float g0, g1, g2;
                     draw3<KIND>(td, lc, rd, g0, g1, g2);
