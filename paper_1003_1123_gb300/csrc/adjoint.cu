@@ -273,10 +273,10 @@ extern "C" int ld_backward(ld_system* sys, int64_t n_steps, int ckpt_every, floa
     const int64_t nseg = (n_steps + P - 1) / P;
     const int SW = h->kind == GBRNG_TAUS ? 4 : 35;
     const size_t ck_bytes = sizeof(float) * (size_t)nseg * (6 + SW) * (size_t)n;
-    // the whole run's noise (12 B per oscillator-step) when it fits the limit,
-    // else one segment's
-    // (the scratch stays with the handle for the next call; the automatic
-    // limit counts what the handle already holds as free)
+    // Noise buffer: the whole run's (12 B per oscillator-step) when it fits
+    // the limit, else one segment's.  The scratch stays with the handle for
+    // the next call (this call synchronises its stream before returning), and
+    // the automatic limit counts what the handle already holds as free.
     const size_t hist_bytes = sizeof(float) * 3 * (size_t)n_steps * (size_t)n;
     const size_t seg_bytes = sizeof(float) * (size_t)P * 3 * (size_t)n;
     int64_t limit = g_hist_limit.load();
