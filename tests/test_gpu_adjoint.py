@@ -160,3 +160,27 @@ def test_history_limit_rejects_bad_values(G):
     with pytest.raises(G.GbrngError):
         G.ld_set_adjoint_history_limit(-2)
     G.ld_set_adjoint_history_limit(-1)
+
+
+def test_scratch_kept_by_the_handle_across_calls(G):
+    """Successive ld_backward calls on one handle (the scratch grows, then is
+    reused by smaller calls, on both noise paths) give what a fresh handle
+    started from the same state gives."""
+    n = 500
+    Kper = W.spring_constants(n, 7, 0.5, 2.0)
+    x0, v0 = W.initial_state(n, 23)
+    s = make(G, "taus", n, 33, Kper, start=(x0, v0))
+    try:
+        for steps, ckpt, limit in ((200, 50, -1), (1200, 100, -1), (300, 30, 0), (90, 20, -1)):
+            G.ld_set_adjoint_history_limit(limit)
+            state = G.rng_get_state(s.rng)
+            xs, vs = s.x.cpu().numpy().copy(), s.v.cpu().numpy().copy()
+            r = G.ld_backward(s, steps, ckpt)
+            f = make(G, "taus", n, 33, Kper, start=(xs, vs))
+            G.rng_set_state(f.rng, state)
+            rf = G.ld_backward(f, steps, ckpt)
+            assert torch.equal(r["dK"], rf["dK"])
+            assert (r["loss"], r["dgamma"], r["dkT"]) == (rf["loss"], rf["dgamma"], rf["dkT"])
+            assert torch.equal(s.x, f.x) and torch.equal(s.v, f.v)
+    finally:
+        G.ld_set_adjoint_history_limit(-1)
