@@ -68,6 +68,11 @@ FILL_BYTES_PER_NUMBER = 4
 # A Lagged Fibonacci fill number: 2 lag reads + 1 ring write + 1 output write
 # of 4 B, all through L2 (the ring stays there; the output streams on to HBM).
 LFG_FILL_BYTES_PER_NUMBER = 16
+# DRAM bytes (read + written) of one launch of a part's kernel from the ncu
+# capture summarised in profiles/ (same kernel, same launch shape), keyed by
+# part and the batched tuner's (T, K, steps per launch); reported as the
+# roofline's `traffic` only when this run chose that shape.
+NCU_TRAFFIC = {("batched_taus", (64, 2, 0)): 302.803456e6 + 237.171456e6}
 
 
 def load_peaks():
@@ -278,6 +283,10 @@ def run_gpu(args, rank, world, dist):
     units_of = {name: units for name, units, _ in parts}
     l2_gbs = measure_l2_copy_gbs(torch)
     roof = roofline(dom, dom_ms, units_of[dom], peaks, peak_src, clk, l2_gbs)
+    roof["traffic"] = NCU_TRAFFIC.get((dom, tuple(G.ld_batched_tune(wl.batch))))
+    if roof["traffic"] is not None:
+        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of "
+                                  "the same kernel and shape (profiles/batched_taus_512sys_5000.md)")
     per_part = {name: {"ms": round(part_ms[name] / args.steps, 4)} for name in part_ms}
     for name in part_ms:
         r = roofline(name, part_ms[name] / args.steps, units_of[name], peaks, peak_src, clk, l2_gbs)
