@@ -356,3 +356,21 @@ def test_allocation_failure_reports_enomem(G):
     assert e.value.code == -2
     r = G.rng_init("taus", 1, 100)
     assert G.rng_fill_u32(r, 1000).numel() == 1000
+
+
+@pytest.mark.parametrize("kind", ["taus", "lcg"])
+def test_two_oscillators_a_thread_odd_n(G, kind):
+    """N = 200001 (odd, enough oscillators for two a thread): the last pair
+    has no second oscillator; full trajectories within the tolerance of the
+    binary32 oracle, generator states bit-exact, per-oscillator K."""
+    n, steps = 200_001, 60
+    Kper = W.spring_constants(n, 41)
+    s, g, p = make_pair(G, kind, n, 52, Kper=Kper)
+    G.ld_init_equilibrium(s)
+    xo, vo = oracle.ld_init_eq_f32(g, n, p, Kper=Kper)
+    st = G.ld_run(s, steps)
+    ost = oracle.ld_run_f32(g, xo, vo, p, steps, Kper=Kper)
+    assert rel_err(s.x.cpu().numpy(), xo) < TRAJ_TOL and rel_err(s.v.cpu().numpy(), vo) < TRAJ_TOL
+    assert math.isclose(st["energy_time_avg"], ost["energy_time_avg"], rel_tol=1e-5)
+    assert math.isclose(st["sum_x2"], ost["sum_x2"], rel_tol=1e-5)
+    assert G.parse_state(G.rng_get_state(s.rng))[1] == oracle_state_bytes(g)
