@@ -244,7 +244,9 @@ static int launch_ld(const ld_system* s, int64_t n_steps, bool want_stats, int64
     DevInfo di;
     GB_CHECK(dev_info(h->device, &di));
     int T = 128;
-    if (s->n < (int64_t)di.sms * 128 * 2) T = 32;   // spread small systems over all SMs
+    // one-warp blocks spread small systems over all SMs, and are 1% faster for
+    // Ran2 at any size (25 warps a SM at 79 registers)
+    if (s->n < (int64_t)di.sms * 128 * 2 || KIND == GBRNG_RAN2) T = 32;
     const size_t smem = KIND == GBRNG_RAN2 ? sizeof(int32_t) * 32 * T : 0;
     int occ = 0;
     GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ld_pt_kernel<KIND, INIT>, T, smem));
