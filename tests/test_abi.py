@@ -69,3 +69,8 @@ def test_invalid_arguments_rejected_before_any_device_work(G):
     assert lib.rng_fill_u32(None, None, 10, None) == -1
     assert lib.rng_set_wait_limit_ns(0) == -1
     assert lib.rng_set_wait_limit_ns(2_000_000_000) == 0
+    assert lib.ld_set_adjoint_history_limit(-2) == -1
+    assert "history limit" in G.gbrng_last_error()
+    assert lib.ld_set_adjoint_history_limit(0) == 0
+    assert lib.ld_set_adjoint_history_limit(-1) == 0
+    assert lib.ld_backward(None, 10, 100, None, None, None, None, None) == -1
