@@ -388,7 +388,11 @@ def compare_paths(wl, G, torch, part_ms, steps):
 def run_e2e(args, wl, parts, G, torch):
     """The same step with inputs in pinned host memory: x, v of every fused
     system copied host->device before and device->host after its run (plus
-    its statistics); each fill's first 4 KiB read back to the host."""
+    its statistics); each fill's first 4 KiB read back to the host.  Every
+    part's device buffers are its own, so each step issues all the inputs on
+    a copy stream at once, each part waits only for its own, and its results
+    go back on a second copy stream while the later parts compute; the step
+    ends when every copy has landed."""
     host = {}
     for kind, s in wl.systems.items():
         host[kind] = (s.x.cpu().pin_memory(), s.v.cpu().pin_memory())
@@ -396,44 +400,59 @@ def run_e2e(args, wl, parts, G, torch):
     host_adj = (wl.adj.x.cpu().pin_memory(), wl.adj.v.cpu().pin_memory(),
                 torch.empty(ADJ_N, dtype=torch.float32).pin_memory())
     probe = torch.empty(1024, dtype=torch.float32).pin_memory()
+    main = torch.cuda.current_stream()
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def inputs(name):
+        """(device, pinned host) pairs a part reads."""
+        if name.startswith("batched"):
+            return [(wl.batch_x, host_batch[0]), (wl.batch_v, host_batch[1])]
+        if name.startswith("adjoint"):
+            return [(wl.adj.x, host_adj[0]), (wl.adj.v, host_adj[1])]
+        if name.startswith("ld_"):
+            s = wl.systems[name[3:]]
+            return [(s.x, host[name[3:]][0]), (s.v, host[name[3:]][1])]
+        return []
+
+    def outputs(name):
+        """(pinned host, device) pairs a part's results go to, and the bytes
+        of host-side statistics its call returns."""
+        if name.startswith("batched"):
+            return [(host_batch[0], wl.batch_x), (host_batch[1], wl.batch_v)], 40 * len(wl.batch)
+        if name.startswith("adjoint"):
+            return [(host_adj[2], wl.dK)], 24
+        if name.startswith("ld_"):
+            s = wl.systems[name[3:]]
+            return [(host[name[3:]][0], s.x), (host[name[3:]][1], s.v)], 40
+        return [(probe, wl.out[:1024])], 0
+
     h2d = d2h = 0
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         h2d = d2h = 0
+        ready = {}
+        with torch.cuda.stream(s_in):
+            for name, _, _ in parts:
+                for dev, hst in inputs(name):
+                    dev.copy_(hst, non_blocking=True)
+                    h2d += hst.numel() * 4
+                ready[name] = torch.cuda.Event()
+                ready[name].record(s_in)
         for name, _, fn in parts:
-            if name.startswith("batched"):
-                hx, hv = host_batch
-                wl.batch_x.copy_(hx, non_blocking=True)
-                wl.batch_v.copy_(hv, non_blocking=True)
-                h2d += 2 * hx.numel() * 4
-                fn()
-                hx.copy_(wl.batch_x, non_blocking=True)
-                hv.copy_(wl.batch_v, non_blocking=True)
-                d2h += 2 * hx.numel() * 4 + 40 * len(wl.batch)
-            elif name.startswith("adjoint"):
-                hx, hv, hd = host_adj
-                wl.adj.x.copy_(hx, non_blocking=True)
-                wl.adj.v.copy_(hv, non_blocking=True)
-                h2d += 2 * hx.numel() * 4
-                fn()
-                hd.copy_(wl.dK, non_blocking=True)
-                d2h += hd.numel() * 4 + 24
-            elif name.startswith("ld_"):
-                kind = name[3:]
-                s = wl.systems[kind]
-                hx, hv = host[kind]
-                s.x.copy_(hx, non_blocking=True)
-                s.v.copy_(hv, non_blocking=True)
-                fn()
-                hx.copy_(s.x, non_blocking=True)
-                hv.copy_(s.v, non_blocking=True)
-                h2d += 2 * hx.numel() * 4
-                d2h += 2 * hx.numel() * 4 + 40
-            else:
-                fn()
-                probe.copy_(wl.out[:1024], non_blocking=True)
-                d2h += 4096
+            main.wait_event(ready[name])
+            fn()
+            done = torch.cuda.Event()
+            done.record(main)
+            s_out.wait_event(done)
+            pairs, stat_bytes = outputs(name)
+            # the fills share one output buffer: their 4 KiB probe is read on
+            # the compute stream, before the next fill overwrites it
+            with torch.cuda.stream(s_out if name.startswith(("ld_", "batched", "adjoint")) else main):
+                for hst, dev in pairs:
+                    hst.copy_(dev, non_blocking=True)
+                    d2h += hst.numel() * 4
+            d2h += stat_bytes
         torch.cuda.synchronize()
     sec = (time.perf_counter() - t0) / args.steps
     osc = sum(p[1] for p in parts)
