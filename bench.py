@@ -617,6 +617,25 @@ def _sample_text(scale, workers=1):
             f"systems at the Taus rate); extrapolated per unit to the full step")
 
 
+def host_cpu() -> str:
+    """The host's architecture and core model, as the kernel reports it
+    (x86 "model name"; Arm implementer and part numbers)."""
+    import platform
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            info = {}
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    info.setdefault(k.strip(), v.strip())
+        model = info.get("model name") or " ".join(
+            f"{k} {info[k]}" for k in ("CPU implementer", "CPU part") if k in info)
+    except OSError:
+        pass
+    return f"{platform.machine()} {model}".strip()
+
+
 def cpu_baseline(parts, part_ms, steps):
     """The oracle on all host cores (spawned processes over independent
     streams), and on one core for reference."""
@@ -630,7 +649,8 @@ def cpu_baseline(parts, part_ms, steps):
     one = _oracle_rates(1.0)
     units = _step_osc_steps(_step_units())
     return {"value": units / _cpu_step_seconds(rates), "unit": "oscillator-steps/s",
-            "cores": workers, "kind": "oracle", "sample": _sample_text(1.0, workers),
+            "cores": workers, "cpu": host_cpu(), "kind": "oracle",
+            "sample": _sample_text(1.0, workers),
             "parts": {k: v for k, v in rates.items()},
             "one_core": {"value": units / _cpu_step_seconds(one), "cores": 1,
                          "parts": {k: v for k, v in one.items()}}}
@@ -664,7 +684,8 @@ def run_reference(args, world):
         "data": "synthetic (seeded oscillators; equilibrium start)",
         "config": {"workload": WORKLOAD, "timed_wall_s": wall},
         "cpu_baseline": {"value": value, "unit": "oscillator-steps/s", "cores": workers,
-                         "kind": "oracle", "sample": _sample_text(scale, workers)},
+                         "cpu": host_cpu(), "kind": "oracle",
+                         "sample": _sample_text(scale, workers)},
         "e2e": {"value": value, "unit": "oscillator-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -727,8 +748,9 @@ def run_case(name: str):
 
 
 def run_sweep():
-    """Time per 1000 steps against N for every generator, persistent and paper
-    form (one launch per step), the state bytes per generator, and the share of
+    """Time per 1000 steps against N for every generator (Hybrid Taus, Ran2,
+    Lagged Fibonacci and the LCG), persistent and paper form (one launch per
+    step), the state bytes per generator, and the share of
     a fused step that generating its numbers alone takes (a fill of the same
     count of normals).  Prints one JSON object; not the bench line."""
     import torch
@@ -747,7 +769,7 @@ def run_sweep():
 
     rows = []
     for n in (10**3, 10**4, 10**5, 10**6, 10**7, 10**8):
-        for kind in KINDS:
+        for kind in KINDS + ("lcg",):
             r = G.rng_init(kind, SEED, n)
             x = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
             v = torch.zeros_like(x)

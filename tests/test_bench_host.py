@@ -56,3 +56,8 @@ def test_step_units_and_replica_helpers():
     assert bench.rank_seed(0) != bench.rank_seed(1)
     assert bench.max_over_ranks(3.5, None, "cpu") == 3.5
     assert bench.whole_job_rate(4, 1e9, 500.0) == pytest.approx(8e9)
+
+
+def test_host_cpu_names_the_architecture():
+    import platform
+    assert bench.host_cpu().startswith(platform.machine())
