@@ -286,7 +286,8 @@ def run_gpu(args, rank, world, dist):
     roof["traffic"] = NCU_TRAFFIC.get((dom, tuple(G.ld_batched_tune(wl.batch))))
     if roof["traffic"] is not None:
         roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of "
-                                  "the same kernel and shape (profiles/batched_taus_512sys_5000.md)")
+                                  "the same kernel and launch shape (committed batched-kernel "
+                                  "profile summary)")
     per_part = {name: {"ms": round(part_ms[name] / args.steps, 4)} for name in part_ms}
     for name in part_ms:
         r = roofline(name, part_ms[name] / args.steps, units_of[name], peaks, peak_src, clk, l2_gbs)
