@@ -292,6 +292,25 @@ def test_lfg_ring_matches_linear_history():
         assert np.array_equal(g.ring_in_order(), np.array(hist[-ll:], np.uint32))
 
 
+def test_lfg_ring_matches_linear_history_random_lags_and_splits():
+    """The same identity for 40 random lag pairs (sl < ll up to 300) and fills
+    split at random lengths (including zero and lengths beyond several ll):
+    the ring position carried across calls never loses or repeats a value."""
+    rng = np.random.default_rng(77)
+    for _ in range(40):
+        ll = int(rng.integers(2, 300))
+        sl = int(rng.integers(1, ll))
+        g = oracle.Gen.custom_lfg(int(rng.integers(0, 2**31)), sl, ll)
+        hist = [int(v) for v in g.state]
+        got = []
+        for _ in range(int(rng.integers(1, 6))):
+            got += [int(v) for v in g.fill_u32(int(rng.integers(0, 4 * ll)))]
+        for p in range(len(got)):
+            hist.append((hist[p] + hist[p + sl]) % 2**32)
+        assert got == hist[ll:]
+        assert np.array_equal(g.ring_in_order(), np.array(hist[-ll:], np.uint32))
+
+
 def test_lfg_default_row_selection():
     """Table I picks a row by system size; with 4 numbers per thread per step
     the row needs sl > 4N and ll - sl > 4N, else the last row (reading)."""
