@@ -156,6 +156,78 @@ def test_ran2_output_range_and_shuffle_conservation():
         assert sorted(iv0 + produced) == sorted(retrieved + st[3:].tolist())
 
 
+NDIV = 1 + (M1 - 1) // 32
+
+
+def _band_repeat_violations(outputs, idums, idum2s):
+    """A consequence of the Bays-Durham shuffle (Knuth, TAOCP vol. 2, Sec.
+    3.2.2, Algorithm B; the draw of Algorithm 2) that needs no table state:
+    the slot a draw reads and refills is the one the previous output selects,
+    so when outputs y_{n-1} and y_n fall in the same band floor(y / NDIV),
+    draw n+1 reads back the idum that draw n stored there:
+        y_{n+1} = idum_n - idum2_{n+1}   (wrapped into [1, m1-1]).
+    Returns (band repeats seen, repeats where that fails)."""
+    seen = bad = 0
+    for n in range(1, len(outputs) - 1):
+        if outputs[n - 1] // NDIV != outputs[n] // NDIV:
+            continue
+        seen += 1
+        want = idums[n] - idum2s[n + 1]
+        if want < 1:
+            want += M1 - 1
+        bad += outputs[n + 1] != want
+    return seen, bad
+
+
+def _lcg_sequence(x, a, m, n):
+    out = []
+    for _ in range(n):
+        x = (a * x) % m
+        out.append(x)
+    return out
+
+
+def test_ran2_shuffle_slot_chosen_by_previous_output():
+    """Algorithm 2's draw takes the table slot from the previous output iy
+    (j = iy / NDIV before iy is replaced).  Pinned from outside the oracle's
+    formula: its outputs, with idum and idum2 recomputed here as plain
+    multiplicative LCG sequences, satisfy the band-repeat property above at
+    every repeat, while CPU models of the same draw that take the slot from
+    the new idum, the new idum2 or the old idum fail it at most repeats."""
+    draws = 20000
+    g = oracle.Gen("ran2", 4242, 2)
+    for s in range(2):
+        st = g.state[s].copy()
+        init = st.copy()
+        outs = [int(st[2])] + [int(oracle.ran2_next(st)) for _ in range(draws)]
+        idums = [int(init[0])] + _lcg_sequence(int(init[0]), A1, M1, draws)
+        idum2s = [int(init[1])] + _lcg_sequence(int(init[1]), A2, M2, draws)
+        seen, bad = _band_repeat_violations(outs, idums, idum2s)
+        assert seen > draws // 64 and bad == 0, (seen, bad)
+
+    # planted mistakes (CPU models, not the oracle): the slot from another word
+    def mutant(pick):
+        st = [int(v) for v in init]
+        iv = st[3:]
+        idum, idum2, iy = st[0], st[1], st[2]
+        outs = [iy]
+        for _ in range(draws):
+            old_idum = idum
+            idum = (A1 * idum) % M1
+            idum2 = (A2 * idum2) % M2
+            j = {"idum": idum, "idum2": idum2, "old_idum": old_idum}[pick] // NDIV
+            iy = iv[j] - idum2
+            iv[j] = idum
+            if iy < 1:
+                iy += M1 - 1
+            outs.append(iy)
+        return outs
+
+    for pick in ("idum", "idum2", "old_idum"):
+        seen, bad = _band_repeat_violations(mutant(pick), idums, idum2s)
+        assert seen > draws // 64 and bad > seen // 2, (pick, seen, bad)
+
+
 def test_ran2_init_warmup():
     """Algorithm 2's seeding: idum2 = seed, NTAB+8 Schrage steps, the last NTAB
     stored with iv[j] at j = NTAB-1 .. 0; iy starts as iv[0] (reading)."""
