@@ -290,22 +290,30 @@ int ld_backward(ld_system* sys, int64_t n_steps, int ckpt_every, float* dK_per,
 int ld_set_adjoint_history_limit(int64_t bytes);
 
 /* ld_run for callers that cannot allocate device memory when they step a
- * system: work recorded under CUDA stream capture (cudaMalloc is not a stream
- * operation), real-time loops that must not wait on the allocator, and hosts
- * that give the library a fixed memory budget.  ld_run may allocate or grow the
- * handle's scratch on any call; this entry point performs the same run for the
- * per-thread generators (Hybrid Taus, Ran2) with the same arguments and
- * results, and allocates nothing.  (The paper has no counterpart: it is a
- * property of this library's memory management.)
- * Its scratch is a fixed static device array of 4096 x 4 + 4 doubles (about
- * 128 KiB) that every GPU which loads the library holds until the process
- * exits; a launch that would need more than 4096 blocks of partial sums is
- * rejected with GBRNG_EINVAL (a GB300 launch uses at most 152 x 16).  The first
- * call on a device looks up the array's device address (with that device
- * current, which must be the generator's device): make that first call before
- * any stream capture.  All calls share the array and each overwrites what it
- * reads, so calls whose GPU work overlaps (other streams, other threads) race;
- * serialise them.  Other requirements and errors as ld_run. */
+ * system.  ld_run may allocate or grow the handle's scratch with cudaMalloc on
+ * any call, and some callers cannot allow that: a real-time loop cannot let a
+ * step wait on cudaMalloc, which may synchronise the device; an application
+ * that gives the library a fixed memory budget, or owns all device memory
+ * through its own pool, has no room for allocations it did not make.  This
+ * entry point performs the same run for the per-thread generators (Hybrid
+ * Taus, Ran2) with the same arguments and results, and allocates nothing.
+ * (The paper has no counterpart: it is a property of this library's memory
+ * management.)
+ * Its scratch is a fixed static device array of 8192 x 4 + 4 doubles (about
+ * 256 KiB) that every GPU which loads the library holds until the process
+ * exits; a launch that would need more than 8192 blocks of partial sums is
+ * rejected with GBRNG_EINVAL (a launch uses at most SMs x 32 blocks, 4864 on a
+ * GB300).  The first call on a device looks up the array's device address
+ * (with that device current, which must be the generator's device) and keeps
+ * it for the process: make that first call before any stream capture, and do
+ * not call it again on a device after cudaDeviceReset.  All calls share the
+ * array and each overwrites what it reads, so calls whose GPU work overlaps
+ * (other streams, other threads) race; serialise them.  out_host non-NULL
+ * reads the statistics back and synchronises the stream (the host waits for
+ * the run); on a stream in capture mode that is refused with GBRNG_EINVAL
+ * before any work is queued.  It runs one oscillator a thread, so Hybrid Taus
+ * systems that fill a resident wave run about 4% slower than in ld_run, which
+ * takes two.  Other requirements and errors as ld_run. */
 int ld_run_noalloc(ld_system* sys, int64_t n_steps, ld_stats* out_host, void* stream);
 
 /* ----------------------------------------------------------------- errors */

@@ -3,13 +3,14 @@
 //
 // ld_run keeps a small scratch area in the generator handle (one slot of
 // partial sums per CTA plus the final statistics) and allocates or grows it
-// with cudaMalloc on demand.  That is a problem for code that steps its system
-// where allocation is not allowed or not wanted: work recorded under CUDA
-// stream capture (cudaMalloc is not a stream operation and breaks a global
-// capture), real-time loops that cannot block on the allocator, and host
-// applications that give the library a fixed memory budget of their own.
+// with cudaMalloc on demand.  Some callers cannot allow that: a real-time loop
+// cannot let a step wait on cudaMalloc, which may synchronise the device; an
+// application that hands the library a fixed memory budget, or owns all device
+// memory through its own pool, has no room for allocations it did not make;
+// and code that runs where CUDA forbids allocation has no way to make one.
 // This file runs the same per-oscillator computation with its scratch in a
 // file-scope device array of fixed size, so a call allocates nothing.
+#include <algorithm>
 #include <mutex>
 
 #include "device.cuh"
@@ -21,7 +22,7 @@ namespace gb {
 // belongs to every GPU that loads the library until the process exits, and it
 // is shared by all calls: each call overwrites the slots it reads (nothing
 // needs to start at zero), so two calls whose work overlaps on the GPU race.
-constexpr int kNoallocMaxBlocks = 4096;
+constexpr int kNoallocMaxBlocks = 8192;
 static __device__ __align__(256) double g_noalloc_scratch[4 * kNoallocMaxBlocks + 4];
 
 struct NoallocArgs {
@@ -36,8 +37,9 @@ struct NoallocArgs {
     double* scratch;   // device address of g_noalloc_scratch
 };
 
+// Same register budget as ld_run's per-thread kernel (six 128-thread blocks per SM).
 template <int KIND>
-__global__ void __launch_bounds__(128) ld_noalloc_kernel(NoallocArgs a)
+__global__ void __launch_bounds__(128, 6) ld_noalloc_kernel(NoallocArgs a)
 {
     extern __shared__ int32_t tab[];   // Ran2: [32][blockDim.x]
     __shared__ double red[4 * 32];
@@ -116,6 +118,9 @@ __global__ void noalloc_finish_kernel(double* scratch, int64_t blocks)
 // Per-device setup, done once with that device current: the device address of
 // the scratch array (in host code its name is only a host-side stand-in) and
 // the SM count.  Fixed-size table, so the lookup allocates nothing either.
+// The cached address belongs to the device's context at the first call: after
+// cudaDeviceReset the module may load at another address, so a process that
+// resets a device must not call ld_run_noalloc on it again.
 constexpr int kNoallocMaxDevices = 64;
 static std::mutex g_noalloc_mu;
 static double* g_noalloc_ptr[kNoallocMaxDevices];
@@ -164,12 +169,25 @@ extern "C" int ld_run_noalloc(ld_system* sys, int64_t n_steps, ld_stats* out_hos
     double* scratch = nullptr;
     int sms = 0;
     GB_CHECK(noalloc_setup(dev, &scratch, &sms));
+    if (out_host) {
+        // the statistics are read back with a stream synchronisation, which a
+        // stream in capture mode does not allow: refuse before queueing work
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        GB_CUDA(cudaStreamIsCapturing(st, &cs));
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(GBRNG_EINVAL,
+                        "ld_run_noalloc: out_host synchronises the stream, which is capturing");
+    }
     if (sys->n == 0) {
         if (out_host) *out_host = ld_stats{0, 0, 0, 0, n_steps};
         return GBRNG_OK;
     }
+    // ld_run's grid shape for one oscillator a thread: one-warp blocks for Ran2
+    // and small systems, else 128 threads; one full resident wave, fewer blocks
+    // only when the system has fewer oscillators than that wave has threads
+    // (at most SMs x 32 blocks: 4864 on a GB300, below the scratch's 8192).
     int T = 128;
-    if (sys->n < (int64_t)sms * 128 * 2) T = 32;
+    if (sys->n < (int64_t)sms * 128 * 2 || h->kind == GBRNG_RAN2) T = 32;
     const size_t smem = h->kind == GBRNG_RAN2 ? sizeof(int32_t) * 32 * T : 0;
     int occ = 0;
     if (h->kind == GBRNG_TAUS)
@@ -177,9 +195,8 @@ extern "C" int ld_run_noalloc(ld_system* sys, int64_t n_steps, ld_stats* out_hos
     else
         GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ld_noalloc_kernel<GBRNG_RAN2>, T, smem));
     if (occ < 1) occ = 1;
-    const int64_t wave = (int64_t)sms * occ * T;
-    const int64_t per_thread = (sys->n + wave - 1) / wave;
-    const int64_t blocks = (sys->n + per_thread * T - 1) / (per_thread * T);
+    int64_t blocks = std::min<int64_t>((int64_t)sms * occ, (sys->n + T - 1) / T);
+    if (blocks < 1) blocks = 1;
     if (blocks > kNoallocMaxBlocks)
         return fail(GBRNG_EINVAL,
                     "ld_run_noalloc: this launch needs %lld blocks of scratch, the fixed array "

@@ -66,6 +66,7 @@ def test_invalid_arguments_rejected_before_any_device_work(G):
     assert lib.rng_init(None, 0, 1, 10, None) == -1
     assert lib.rng_init_lfg(C.byref(h), 1, 10, 11, None) == -5
     assert lib.ld_run(None, 10, None, None) == -1
+    assert lib.ld_run_noalloc(None, 10, None, None) == -1
     assert lib.rng_fill_u32(None, None, 10, None) == -1
     assert lib.rng_set_wait_limit_ns(0) == -1
     assert lib.rng_set_wait_limit_ns(2_000_000_000) == 0

@@ -1,7 +1,8 @@
-"""ld_run_noalloc — the run for callers that cannot allocate device memory when
-they step a system (stream capture, real-time loops, fixed memory budgets) —
-gives the same results as ld_run.  Collected last on purpose: a failure here
-comes after every other test has run."""
+"""ld_run_noalloc is the run for callers that cannot allocate device memory
+when they step a system: a real-time loop that cannot wait on cudaMalloc, or
+an application that gives the library a fixed memory budget.  It must give
+the same results as ld_run.  This file is collected last on purpose, so a
+failure here comes after every other test has run."""
 import math
 
 import numpy as np
@@ -60,3 +61,16 @@ def test_noalloc_matches_ld_run_twice(G, kind, n):
             assert math.isclose(a[k], b[k], rel_tol=STATS_RTOL), (k, a[k], b[k])
         assert abs(a["sum_xv"] - b["sum_xv"]) <= STATS_RTOL * math.sqrt(a["sum_x2"] * a["sum_v2"])
         assert b["steps"] == steps
+
+
+@pytest.mark.parametrize("kind", ["taus", "ran2"])
+def test_noalloc_empty_system(G, kind):
+    """n == 0: nothing to run; the statistics are zero and the step count is
+    reported, as ld_run does."""
+    r = G.rng_init(kind, 5, 1)
+    x = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    s = G.LdSystem(r, x, torch.zeros_like(x), K=1.0, m=1.0, gamma=0.5, kT=1.0, dt=0.01)
+    for _ in range(2):
+        b = G.ld_run_noalloc(s, 7)
+        assert b["steps"] == 7
+        assert b["sum_x2"] == b["sum_v2"] == b["sum_xv"] == b["energy_time_avg"] == 0.0
