@@ -8,10 +8,14 @@ workload (10^6 independent 3-D oscillators, the paper's Sec. IV test shape):
   - stand-alone fills of 2^30 uniform and 2^30 normal binary32 numbers per
     generator;
   - 512 uneven systems (N log-uniform in [1e2, 1e5]) x 5000 steps in one
-    batched graph launch, and the adjoint of 1e5 oscillators x 1e4 steps.
+    batched graph launch, and the adjoint of 1e5 oscillators x 1e4 steps for
+    Hybrid Taus and Ran2 (noise regenerated from checkpoints every 100 steps).
 value = oscillator-steps advanced per second over the whole step (fills
 count toward the time, not the oscillator-steps).  Inputs stay resident in
 HBM; the L2 (126 MB) is flushed by a 256 MiB write before every timed part.
+After the timed steps, the large workload (10^8 oscillators x 1000 steps per
+generator) is timed once per generator, outside the step, and reported per
+part with its roofline.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbrng|reference]
 
@@ -44,25 +48,41 @@ L2_FLUSH_BYTES = 256 << 20
 PARAMS = dict(K=1.0, m=1.0, gamma=0.5, kT=1.0, dt=0.01)
 BATCH_SYSTEMS, BATCH_STEPS = 512, 5000
 ADJ_N, ADJ_STEPS, ADJ_CKPT = 10**5, 10**4, 100
+ADJ_KINDS = ("taus", "ran2")
+LARGE_N, LARGE_STEPS = 10**8, 1000
+LARGE_PARAMS = dict(K=1.0, m=1.0, gamma=1.0, kT=1.0, dt=0.01)
 STEPWISE_STEPS = 1000
 WORKLOAD = ("N=1e6 3-D oscillators x 1e4 fused steps per generator (Taus, Ran2, Lagged "
             "Fibonacci row 9) + 2^30 uniform and 2^30 normal fills per generator + 512 uneven "
-            "systems (N 1e2..1e5) x 5000 batched steps + adjoint of 1e5 oscillators x 1e4 steps")
+            "systems (N 1e2..1e5) x 5000 batched steps + adjoint (Taus, Ran2) of 1e5 "
+            "oscillators x 1e4 steps")
 
-# Integer operations per oscillator-step that the generators themselves
-# require (four draws), one per operator of the algorithm:
-#   Hybrid Taus: 3 components x 6 shift/logic ops + LCG multiply and add (2)
-#                + 3 combining xors = 23 per draw -> 92;
-#   Ran2: 2 Schrage steps x 8 (quotient, 3 multiplies, 2 subtracts, compare,
-#         add) + shuffle (index quotient, subtract, compare, add, table load
-#         and store) 6 = 22 per draw -> 88.
-INT_OPS_PER_OSC_STEP = {"taus": 92, "ran2": 88}
+# Minimal integer-ALU-pipe instructions a draw needs, given the instruction
+# set (LOP3 evaluates any three-input logic function, SHF is one shift, and
+# left shifts, multiplies and adds can run as IMAD on the FMA pipe instead):
+#   Hybrid Taus, per Tausworthe word ((y << s1) ^ y) >> s2, ((y & c) << s3) ^ b:
+#     the xor (LOP3), the right shift (SHF) and the masked xor (LOP3) = 3, the
+#     two left shifts on IMAD; 3 words = 9, the LCG word one IMAD (FMA pipe),
+#     the four-way xor 2 LOP3 -> 11 per draw, 44 per oscillator-step;
+#   Ran2, per a*x mod m from the 64-bit product (IMAD.WIDE on the FMA pipe):
+#     the 31-bit funnel shift of the product (SHF), the low-bit mask (LOP3) and
+#     the conditional subtraction as an unsigned min of r and r - m (IMNMX) = 3,
+#     two of them 6; the slot index iy / NDIV (multiply-high on IMAD, one SHF)
+#     1; the wrap of iy as min_u32(y, y + m1 - 1) 1 -> 8 per draw, 32 per
+#     oscillator-step.
+# A lower bound on the work of the 64-lane ALU pipe, so no part can read above
+# 1.0 against it; ncu's measured ALU-pipe utilisation is reported beside it.
+INT_OPS_PER_DRAW = {"taus": 11, "ran2": 8}
+INT_OPS_PER_OSC_STEP = {k: 4 * v for k, v in INT_OPS_PER_DRAW.items()}
 # Algorithmic bytes per oscillator-step of the Lagged Fibonacci fused step at
 # 1e6 oscillators: four ring values, each 2 lag reads + 1 write of 4 B = 48 B
 # (x and v stay in shared memory for the whole launch).  The ring (64 MiB for
 # the last Table I row) stays in L2, so the bound is L2 bandwidth, measured
 # below as a device-to-device copy of 2 x 32 MiB that stays L2-resident.
 LFG_BYTES_PER_OSC_STEP = 48
+# At 1e8 oscillators x and v no longer fit on chip: every step reads and
+# writes them (6 binary32 each way), 48 B per oscillator-step of HBM traffic.
+LFG_XV_BYTES_PER_OSC_STEP = 48
 L2_COPY_BYTES = 32 << 20
 FILL_BYTES_PER_NUMBER = 4
 # A Lagged Fibonacci fill number: 2 lag reads + 1 ring write + 1 output write
@@ -73,6 +93,11 @@ LFG_FILL_BYTES_PER_NUMBER = 16
 # part and the batched tuner's (T, K, steps per launch); reported as the
 # roofline's `traffic` only when this run chose that shape.
 NCU_TRAFFIC = {("batched_taus", (64, 2, 0)): 302.803456e6 + 237.171456e6}
+# ncu's ALU-pipe utilisation (sm__pipe_alu_cycles_active, % of peak sustained
+# active) of each ALU-bound part's kernel, from the captures summarised in
+# profiles/ (same kernel and launch shape, smaller step counts).
+NCU_ALU_PIPE_PCT = {"ld_taus": 71.5, "batched_taus": 73.7, "ld_ran2": 55.0,
+                    "fill_uniform_taus": 88.0, "fill_normal_taus": 77.0}
 
 
 def load_peaks():
@@ -200,12 +225,16 @@ class Workload:
             G.ld_init_equilibrium(s)
             self.batch.append(s)
             off += n
-        # adjoint: 1e5 oscillators, K per oscillator, checkpoints every 100 steps
-        ra = G.rng_init("taus", seed + 11, ADJ_N)
-        xa = torch.zeros((ADJ_N, 3), dtype=torch.float32, device="cuda")
-        self.adj = G.LdSystem(ra, xa, torch.zeros_like(xa), K_per=torch.ones(ADJ_N, device="cuda"),
-                              **{k: v for k, v in PARAMS.items() if k != "K"})
-        G.ld_init_equilibrium(self.adj)
+        # adjoint: 1e5 oscillators, K per oscillator, checkpoints every 100
+        # steps, one system per generator
+        self.adj = {}
+        for j, kind in enumerate(ADJ_KINDS):
+            ra = G.rng_init(kind, seed + 11 + j, ADJ_N)
+            xa = torch.zeros((ADJ_N, 3), dtype=torch.float32, device="cuda")
+            sa = G.LdSystem(ra, xa, torch.zeros_like(xa), K_per=torch.ones(ADJ_N, device="cuda"),
+                            **{k: v for k, v in PARAMS.items() if k != "K"})
+            G.ld_init_equilibrium(sa)
+            self.adj[kind] = sa
         self.dK = torch.empty(ADJ_N, dtype=torch.float32, device="cuda")
         torch.cuda.synchronize()
 
@@ -223,8 +252,9 @@ class Workload:
                         lambda r=r: G.rng_fill_normal(r, FILL_N, out=self.out)))
         out.append(("batched_taus", self.batch_osc * BATCH_STEPS,
                     lambda: G.ld_run_batched(self.batch, BATCH_STEPS)))
-        out.append(("adjoint_taus", ADJ_N * ADJ_STEPS,
-                    lambda: G.ld_backward(self.adj, ADJ_STEPS, ADJ_CKPT, dK=self.dK)))
+        for kind in ADJ_KINDS:
+            out.append((f"adjoint_{kind}", ADJ_N * ADJ_STEPS,
+                        lambda s=self.adj[kind]: adjoint_regenerating(G, s, self.dK)))
         return out
 
     def step(self, parts, events):
@@ -233,6 +263,16 @@ class Workload:
             events[i][0].record()
             fn()
             events[i][1].record()
+
+
+def adjoint_regenerating(G, s, dK):
+    """ld_backward with the noise regenerated from the checkpointed generator
+    states (history limit 0), the adjoint's memory-lean form."""
+    G.ld_set_adjoint_history_limit(0)
+    try:
+        return G.ld_backward(s, ADJ_STEPS, ADJ_CKPT, dK=dK)
+    finally:
+        G.ld_set_adjoint_history_limit(-1)
 
 
 def run_gpu(args, rank, world, dist):
@@ -276,7 +316,7 @@ def run_gpu(args, rank, world, dist):
     # ---- end to end through host buffers (pinned inputs and outputs)
     e2e = run_e2e(args, wl, parts, G, torch)
 
-    # ---- roofline of the dominant part
+    # ---- roofline of the dominant part, and of every part
     peaks, peak_src = load_peaks()
     dom = max(part_ms, key=part_ms.get)
     dom_ms = part_ms[dom] / args.steps
@@ -291,8 +331,8 @@ def run_gpu(args, rank, world, dist):
     per_part = {name: {"ms": round(part_ms[name] / args.steps, 4)} for name in part_ms}
     for name in part_ms:
         r = roofline(name, part_ms[name] / args.steps, units_of[name], peaks, peak_src, clk, l2_gbs)
-        per_part[name]["roofline"] = {k: r[k] for k in ("bound", "achieved", "unit", "frac", "alt")
-                                      if k in r}
+        per_part[name]["roofline"] = {k: r[k] for k in ("bound", "achieved", "unit", "frac", "alt",
+                                                         "ncu_alu_pipe_pct") if k in r}
     for name, units, _ in parts:
         if units:
             per_part[name]["osc_steps_per_s"] = units / (part_ms[name] / args.steps / 1e3)
@@ -300,6 +340,12 @@ def run_gpu(args, rank, world, dist):
             per_part[name]["numbers_per_s"] = FILL_N / (part_ms[name] / args.steps / 1e3)
             per_part[name]["GBps"] = FILL_N * 4 / (part_ms[name] / args.steps / 1e3) / 1e9
     extras = compare_paths(wl, G, torch, part_ms, args.steps)
+
+    # ---- the large workload, outside the step: 1e8 oscillators x 1000 steps
+    del wl
+    torch.cuda.empty_cache()
+    large, large_clk = run_large(G, torch, dev, peaks, peak_src, l2_gbs)
+    per_part.update(large)
 
     line = {
         "metric": "oscillator-steps/s (fused LD+RNG, all generators, whole hot path)",
@@ -315,23 +361,89 @@ def run_gpu(args, rank, world, dist):
         "dtype": "f32+u32",
         "data": "synthetic (seeded oscillators; equilibrium start)",
         "config": {"workload": WORKLOAD,
-                   "batched": {"systems": BATCH_SYSTEMS, "oscillators": wl.batch_osc,
+                   "batched": {"systems": BATCH_SYSTEMS, "oscillators": extras["batched_osc"],
                                "steps": BATCH_STEPS},
-                   "adjoint": {"n": ADJ_N, "steps": ADJ_STEPS, "checkpoint_every": ADJ_CKPT},
+                   "adjoint": {"n": ADJ_N, "steps": ADJ_STEPS, "checkpoint_every": ADJ_CKPT,
+                               "noise": "regenerated from checkpoints"},
+                   "large": {"n": LARGE_N, "steps": LARGE_STEPS, "params": LARGE_PARAMS,
+                             "timed": "once per generator after the steps, outside the step"},
                    "n_oscillators": N_OSC, "ld_steps": LD_STEPS, "fill_numbers": FILL_N,
                    "params": PARAMS, "l2": "flushed (256 MiB write) before every part",
                    "parallelism": f"replicas x{world} (independent seeds, no collective)"},
         "clocks": clk,
-        "gpu_launches": gpu_launches(parts, args.steps, G.ld_batched_tune(wl.batch)),
-        "batched_tune": list(G.ld_batched_tune(wl.batch)),
+        "gpu_launches": gpu_launches(parts, args.steps, extras["batched_tune"]),
+        "batched_tune": extras["batched_tune"],
         "e2e": e2e,
         "roofline": roof,
         "parts": per_part,
         "comparisons": extras,
+        "large_clocks": large_clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(parts, part_ms, args.steps)
+    # per-generator headline figures as flat keys of the roofline record (the
+    # metric is quoted per generator), repeated as the line's last key
+    head = headline(per_part)
+    roof.update(head)
+    line["per_generator"] = head
     return line
+
+
+def headline(per_part):
+    """Per-generator fused rates and roofline fractions: the throughput
+    workload (1e6 oscillators), the large one (1e8), the adjoint."""
+    out = {}
+    for name, rec in per_part.items():
+        if not (name.startswith("ld_") or name.startswith("adjoint_")):
+            continue
+        out[f"{name}.osc_steps_per_s"] = rec.get("osc_steps_per_s")
+        r = rec.get("roofline", {})
+        out[f"{name}.frac"] = r.get("frac")
+        out[f"{name}.bound"] = r.get("bound")
+        if "ncu_alu_pipe_pct" in r:
+            out[f"{name}.ncu_alu_pipe_pct"] = r["ncu_alu_pipe_pct"]
+    return out
+
+
+def run_large(G, torch, dev, peaks, peak_src, l2_gbs):
+    """The large workload: 1e8 independent 3-D oscillators x 1000 steps per
+    generator (x, v 2.4 GB; Ran2 state 14 GB), K = gamma = kT = 1, dt = 0.01,
+    one system at a time.  A 100-step warm-up run, then one timed 1000-step
+    run (CUDA events on the launching stream, L2 flushed before it)."""
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(dev)
+    out = {}
+    clocks.start()
+    for kind in KINDS:
+        r = G.rng_init(kind, SEED + 5, LARGE_N)
+        x = torch.zeros((LARGE_N, 3), dtype=torch.float32, device="cuda")
+        v = torch.zeros_like(x)
+        s = G.LdSystem(r, x, v, **LARGE_PARAMS)
+        G.ld_init_equilibrium(s)
+        G.ld_run(s, 100, stats=False)
+        flush.fill_(1.0)
+        a.record()
+        G.ld_run(s, LARGE_STEPS)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        name = f"ld_{kind}_1e8"
+        units = LARGE_N * LARGE_STEPS
+        rf = roofline(name, ms, units, peaks, peak_src, {"sm_mhz": None}, l2_gbs)
+        out[name] = {"ms": round(ms, 3), "osc_steps_per_s": units / (ms / 1e3),
+                     "outside_step": True,
+                     "roofline": {k: rf[k] for k in ("bound", "achieved", "unit", "frac", "alt",
+                                                     "ncu_alu_pipe_pct") if k in rf}}
+        del s, x, v, r
+        torch.cuda.empty_cache()
+    clk = clocks.stop()
+    # fractions against the clock seen during these runs
+    for name, rec in out.items():
+        rf = roofline(name, rec["ms"], LARGE_N * LARGE_STEPS, peaks, peak_src, clk, l2_gbs)
+        rec["roofline"] = {k: rf[k] for k in ("bound", "achieved", "unit", "frac", "alt",
+                                              "ncu_alu_pipe_pct") if k in rf}
+    return out, clk
 
 
 def gpu_launches(parts, steps, batched_tune=None):
@@ -352,33 +464,43 @@ def gpu_launches(parts, steps, batched_tune=None):
 
 def compare_paths(wl, G, torch, part_ms, steps):
     """Outside the timed region: the batched systems run one ld_run each (the
-    per-system alternative the batched graph replaces), and a plain forward
-    run of the adjoint system (the adjoint's cost relative to a forward)."""
+    per-system alternative the batched graph replaces); per adjoint system a
+    plain forward run (the adjoint's cost relative to a forward) and the
+    adjoint keeping the forward run's noise instead of regenerating it; the
+    paper form (one launch per step) on the throughput systems."""
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for s in wl.batch:
         G.ld_run(s, BATCH_STEPS, stats=False)
     torch.cuda.synchronize()
     per_system_ms = 1e3 * (time.perf_counter() - t0)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    G.ld_run(wl.adj, ADJ_STEPS)
-    b.record()
-    torch.cuda.synchronize()
-    fwd_ms = a.elapsed_time(b)
     batched_ms = part_ms["batched_taus"] / steps
-    adj_ms = part_ms["adjoint_taus"] / steps
     out = {"batched_ms": batched_ms, "per_system_launches_ms": per_system_ms,
-           "batched_speedup": per_system_ms / batched_ms,
-           "adjoint_ms": adj_ms, "forward_ms": fwd_ms, "adjoint_over_forward": adj_ms / fwd_ms}
+           "batched_speedup": per_system_ms / batched_ms, "batched_osc": wl.batch_osc,
+           "batched_tune": list(G.ld_batched_tune(wl.batch))}
+    for kind, sa in wl.adj.items():
+        fwd_ms = timed(lambda: G.ld_run(sa, ADJ_STEPS))
+        adj_ms = part_ms[f"adjoint_{kind}"] / steps
+        G.ld_backward(sa, ADJ_STEPS, ADJ_CKPT, dK=wl.dK)      # sizes the history scratch
+        hist_ms = timed(lambda: G.ld_backward(sa, ADJ_STEPS, ADJ_CKPT, dK=wl.dK))
+        out[f"adjoint_{kind}"] = {
+            "regenerating_ms": adj_ms, "forward_ms": fwd_ms,
+            "regenerating_over_forward": adj_ms / fwd_ms,
+            "with_noise_history_ms": hist_ms, "with_noise_history_over_forward": hist_ms / fwd_ms}
     # the paper form (one launch per step, state through global memory) on the
     # same 1e6-oscillator systems, STEPWISE_STEPS steps, per step vs persistent
     for kind, sysm in wl.systems.items():
-        a.record()
-        G.ld_run_stepwise(sysm, STEPWISE_STEPS, stats=False)
-        b.record()
-        torch.cuda.synchronize()
-        sw = a.elapsed_time(b) / STEPWISE_STEPS
+        sw = timed(lambda: G.ld_run_stepwise(sysm, STEPWISE_STEPS, stats=False)) / STEPWISE_STEPS
         pers = part_ms[f"ld_{kind}"] / steps / LD_STEPS
         out[f"stepwise_{kind}_us_per_step"] = 1e3 * sw
         out[f"persistent_{kind}_us_per_step"] = 1e3 * pers
@@ -398,8 +520,9 @@ def run_e2e(args, wl, parts, G, torch):
     for kind, s in wl.systems.items():
         host[kind] = (s.x.cpu().pin_memory(), s.v.cpu().pin_memory())
     host_batch = (wl.batch_x.cpu().pin_memory(), wl.batch_v.cpu().pin_memory())
-    host_adj = (wl.adj.x.cpu().pin_memory(), wl.adj.v.cpu().pin_memory(),
-                torch.empty(ADJ_N, dtype=torch.float32).pin_memory())
+    host_adj = {k: (sa.x.cpu().pin_memory(), sa.v.cpu().pin_memory(),
+                    torch.empty(ADJ_N, dtype=torch.float32).pin_memory())
+                for k, sa in wl.adj.items()}
     probe = torch.empty(1024, dtype=torch.float32).pin_memory()
     main = torch.cuda.current_stream()
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
@@ -409,7 +532,8 @@ def run_e2e(args, wl, parts, G, torch):
         if name.startswith("batched"):
             return [(wl.batch_x, host_batch[0]), (wl.batch_v, host_batch[1])]
         if name.startswith("adjoint"):
-            return [(wl.adj.x, host_adj[0]), (wl.adj.v, host_adj[1])]
+            k = name.split("_")[-1]
+            return [(wl.adj[k].x, host_adj[k][0]), (wl.adj[k].v, host_adj[k][1])]
         if name.startswith("ld_"):
             s = wl.systems[name[3:]]
             return [(s.x, host[name[3:]][0]), (s.v, host[name[3:]][1])]
@@ -421,7 +545,7 @@ def run_e2e(args, wl, parts, G, torch):
         if name.startswith("batched"):
             return [(host_batch[0], wl.batch_x), (host_batch[1], wl.batch_v)], 40 * len(wl.batch)
         if name.startswith("adjoint"):
-            return [(host_adj[2], wl.dK)], 24
+            return [(host_adj[name.split("_")[-1]][2], wl.dK)], 24
         if name.startswith("ld_"):
             s = wl.systems[name[3:]]
             return [(host[name[3:]][0], s.x), (host[name[3:]][1], s.v)], 40
@@ -449,7 +573,8 @@ def run_e2e(args, wl, parts, G, torch):
             pairs, stat_bytes = outputs(name)
             # the fills share one output buffer: their 4 KiB probe is read on
             # the compute stream, before the next fill overwrites it
-            with torch.cuda.stream(s_out if name.startswith(("ld_", "batched", "adjoint")) else main):
+            # (so is the adjoints' shared dK buffer)
+            with torch.cuda.stream(s_out if name.startswith(("ld_", "batched")) else main):
                 for hst, dev in pairs:
                     hst.copy_(dev, non_blocking=True)
                     d2h += hst.numel() * 4
@@ -478,23 +603,45 @@ def measure_l2_copy_gbs(torch):
     return 2 * L2_COPY_BYTES * 50 / (e0.elapsed_time(e1) / 1e3) / 1e9
 
 
+def part_kind(part: str) -> str:
+    """Generator of a part: the kind name among its underscore-separated words."""
+    for k in KINDS:
+        if k in part.split("_"):
+            return k
+    raise ValueError(part)
+
+
 def roofline(part, ms, units, peaks, src, clk, l2_gbs=None):
-    """Roofline of one part against its binding resource.  Taus/Ran2 fused,
-    batched and adjoint work: the INT32 lanes (algorithmic integer ops of the
-    generator: 92 or 88 per oscillator-step; the adjoint draws every number
-    once when it keeps the run's noise, as it does at this size).  Lagged Fibonacci fused steps: the L2 copy bandwidth measured in
-    this run (48 algorithmic bytes per oscillator-step).  Taus/Ran2 fills: the
-    HBM copy bandwidth (4 B per number).  Lagged Fibonacci fills: L2 (16 B per
-    number), with the HBM figure beside it as `alt`."""
+    """Roofline of one part against its binding resource.
+    - Taus/Ran2 fused, batched and adjoint: the 64-lane integer ALU pipe, with
+      the minimal ALU instructions of the generator's draws (INT_OPS_PER_DRAW;
+      four draws an oscillator-step, drawn twice by the adjoint, whose reverse
+      sweep regenerates the noise), and ncu's measured ALU-pipe utilisation
+      beside it where a capture exists.
+    - Lagged Fibonacci fused at 1e6 oscillators: the L2 copy bandwidth measured
+      in this run (48 algorithmic bytes per oscillator-step: four ring values,
+      2 lag reads + 1 write each; x and v stay in shared memory).
+    - Lagged Fibonacci fused at 1e8: HBM (x and v stream every step: 24 B read
+      + 24 B written per oscillator-step), the ring's 48 B in L2 beside it.
+    - Taus/Ran2 fills: the HBM copy bandwidth (4 B per number), with the
+      minimal ALU work beside it; Lagged Fibonacci fills: L2 (16 B per number),
+      with the HBM figure beside it."""
     mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    kind = part.split("_")[-1]
+    kind = part_kind(part)
     sec = ms / 1e3
+    alu_peak = SMS * INT32_LANES_PER_SM * mhz * 1e6 / 1e12
+    alu_src = f"152 SMs x {INT32_LANES_PER_SM} INT32 lanes x {mhz} MHz (median SM clock under load)"
+    ncu = NCU_ALU_PIPE_PCT.get(part)
     if part.startswith("fill_"):
         hbm = FILL_N * FILL_BYTES_PER_NUMBER / sec / 1e9
         r = {"kernel": part, "bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"],
              "unit": "GB/s", "frac": hbm / peaks["hbm_gbs"], "traffic": None,
              "peak_source": f"{src} hbm_gbs (copy bandwidth); 4 B per number"}
         if kind != "lagfib":
+            ops = INT_OPS_PER_DRAW[kind] * FILL_N / sec / 1e12
+            r["alt"] = {"bound": "alu", "achieved": ops, "unit": "Tops/s", "frac": ops / alu_peak}
+            if ncu is not None:
+                r["ncu_alu_pipe_pct"] = ncu
             return r
         l2 = FILL_N * LFG_FILL_BYTES_PER_NUMBER / sec / 1e9
         return {"kernel": part, "bound": "l2", "achieved": l2, "peak": l2_gbs, "unit": "GB/s",
@@ -503,24 +650,36 @@ def roofline(part, ms, units, peaks, src, clk, l2_gbs=None):
                                "16 B per number",
                 "alt": {k: r[k] for k in ("bound", "achieved", "unit", "frac")}}
     if kind == "lagfib":
-        achieved = units * LFG_BYTES_PER_OSC_STEP / sec / 1e9
-        return {"kernel": part, "bound": "l2", "achieved": achieved, "peak": l2_gbs,
-                "unit": "GB/s", "frac": achieved / l2_gbs if l2_gbs else None, "traffic": None,
-                "peak_source": "L2-resident copy of 2 x 32 MiB measured in this run; "
-                               "algorithmic 48 B per oscillator-step"}
-    ops = INT_OPS_PER_OSC_STEP[kind] * units
+        l2 = units * LFG_BYTES_PER_OSC_STEP / sec / 1e9
+        l2r = {"kernel": part, "bound": "l2", "achieved": l2, "peak": l2_gbs,
+               "unit": "GB/s", "frac": l2 / l2_gbs if l2_gbs else None, "traffic": None,
+               "peak_source": "L2-resident copy of 2 x 32 MiB measured in this run; "
+                              "algorithmic 48 B per oscillator-step (ring)"}
+        if not part.endswith("_1e8"):
+            return l2r
+        hbm = units * LFG_XV_BYTES_PER_OSC_STEP / sec / 1e9
+        return {"kernel": part, "bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": hbm / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": f"{src} hbm_gbs (copy bandwidth); x, v read and written every "
+                               "step: 48 B per oscillator-step",
+                "alt": {k: l2r[k] for k in ("bound", "achieved", "unit", "frac")}}
+    draws = 2 if part.startswith("adjoint_") else 1
+    ops = draws * INT_OPS_PER_OSC_STEP[kind] * units
     achieved = ops / sec / 1e12
-    peak = SMS * INT32_LANES_PER_SM * mhz * 1e6 / 1e12
-    return {"kernel": part, "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": "Tops/s", "frac": achieved / peak, "traffic": None,
-            "peak_source": f"152 SMs x {INT32_LANES_PER_SM} INT32 lanes x {mhz} MHz "
-                           f"(median SM clock under load)"}
+    r = {"kernel": part, "bound": "alu", "achieved": achieved, "peak": alu_peak,
+         "unit": "Tops/s", "frac": achieved / alu_peak, "traffic": None,
+         "peak_source": alu_src,
+         "ops_source": f"minimal ALU-pipe instructions: {INT_OPS_PER_DRAW[kind]} per draw, "
+                       f"{4 * draws} draws per oscillator-step"}
+    if ncu is not None:
+        r["ncu_alu_pipe_pct"] = ncu
+    return r
 
 
 # --------------------------------------------------------------------- CPU
 ORACLE_PARTS = ("ld_taus", "ld_ran2", "ld_lagfib", "fill_uniform_taus", "fill_normal_taus",
                 "fill_uniform_ran2", "fill_normal_ran2", "fill_uniform_lagfib",
-                "fill_normal_lagfib", "adjoint_taus")
+                "fill_normal_lagfib", "adjoint_taus", "adjoint_ran2")
 
 
 def _oracle_part(name: str, scale: float, shard: int = 0):
@@ -553,8 +712,8 @@ def _oracle_part(name: str, scale: float, shard: int = 0):
         t0 = time.perf_counter()
         f(nf)
         return nf, time.perf_counter() - t0
-    na, sa = max(8, int(200 * scale)), 1000          # adjoint_taus, FP64
-    g = oracle.Gen("taus", seed + 11, na)
+    na, sa = max(8, int(200 * scale)), 1000          # adjoint_<kind>, FP64
+    g = oracle.Gen(kind, seed + 11, na)
     x, v = oracle.ld_init_eq_f64(g, na, p)
     t0 = time.perf_counter()
     oracle.ld_adjoint_f64(g, x, v, p, sa, Kper=np.ones(na))
@@ -596,7 +755,8 @@ def _step_units():
     units = {f"ld_{k}": N_OSC * LD_STEPS for k in KINDS}
     units.update({f"fill_{m}_{k}": FILL_N for k in KINDS for m in ("uniform", "normal")})
     units["batched_taus"] = batch_osc * BATCH_STEPS
-    units["adjoint_taus"] = ADJ_N * ADJ_STEPS
+    for k in ADJ_KINDS:
+        units[f"adjoint_{k}"] = ADJ_N * ADJ_STEPS
     return units
 
 
@@ -694,7 +854,8 @@ def run_reference(args, world):
 
 CASES = ("ld_taus", "ld_ran2", "ld_lagfib", "fill_uniform_taus", "fill_normal_taus",
          "fill_uniform_ran2", "fill_normal_ran2", "fill_uniform_lagfib", "fill_normal_lagfib",
-         "batched_taus", "adjoint_taus")
+         "batched_taus", "adjoint_taus", "adjoint_ran2", "ld_taus_1e8", "ld_ran2_1e8",
+         "ld_lagfib_1e8")
 
 
 def run_case(name: str):
@@ -703,15 +864,27 @@ def run_case(name: str):
     (1 GiB, larger than L2)."""
     import torch
     from paper_1003_1123_gb300 import gbrng as G
-    kind = name.split("_")[-1]
-    if name == "adjoint_taus":
-        # the bench's adjoint system (1e5 oscillators), 1000 steps, checkpoints every 100
-        r = G.rng_init("taus", SEED + 11, ADJ_N)
+    kind = part_kind(name)
+    if name.startswith("adjoint_"):
+        # the bench's adjoint system (1e5 oscillators), 1000 steps, checkpoints
+        # every 100, noise regenerated as in the bench step
+        r = G.rng_init(kind, SEED + 11, ADJ_N)
         x = torch.zeros((ADJ_N, 3), dtype=torch.float32, device="cuda")
-        s = G.LdSystem(r, x, torch.zeros_like(x), K_per=torch.ones(ADJ_N, device="cuda"), **PARAMS)
+        s = G.LdSystem(r, x, torch.zeros_like(x), K_per=torch.ones(ADJ_N, device="cuda"),
+                       **{k: v for k, v in PARAMS.items() if k != "K"})
         G.ld_init_equilibrium(s)
+        G.ld_set_adjoint_history_limit(0)
         for _ in range(2):
             G.ld_backward(s, 1000, ADJ_CKPT)
+    elif name.endswith("_1e8"):
+        # the large workload at 1e7 oscillators (x, v 240 MB, larger than L2) x 10 steps
+        n = 10**7
+        r = G.rng_init(kind, SEED, n)
+        x = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
+        s = G.LdSystem(r, x, torch.zeros_like(x), **LARGE_PARAMS)
+        G.ld_init_equilibrium(s)
+        for _ in range(2):
+            G.ld_run(s, 10)
     elif name == "batched_taus":
         # the bench's 512 systems; the second graph replay (autotuned shape
         # cached by the first) runs inside the NVTX range "profile"
@@ -768,6 +941,8 @@ def run_sweep():
         torch.cuda.synchronize()
         return ev[0].elapsed_time(ev[1])
 
+    clocks = Clocks(torch.cuda.current_device())
+    clocks.start()
     rows = []
     for n in (10**3, 10**4, 10**5, 10**6, 10**7, 10**8):
         for kind in KINDS + ("lcg",):
@@ -818,7 +993,7 @@ def run_sweep():
         del s, x, r
     return {"sweep": "time per 1000 steps vs N (E2), state bytes (E3), RNG share (E4), "
                      "Table I rows at N = 1000",
-            "params": PARAMS, "rows": rows, "lag_rows": lag_rows}
+            "params": PARAMS, "rows": rows, "lag_rows": lag_rows, "clocks": clocks.stop()}
 
 
 def main():

@@ -1,8 +1,11 @@
 """The large workload: 10^8 independent 3-D oscillators (x, v 2.4 GB; Ran2
 state 14 GB), 1000 steps, K = gamma = kT = 1, dt = 0.01, for every generator.
 Sampled oscillators of the per-thread generators are recomputed by the oracle
-from their own streams; every generator's ensemble moments match the exactly
-propagated covariance of the discrete scheme within 3 sigma."""
+from their own streams; the shared Lagged Fibonacci sequence is compared with
+the oracle on every oscillator over the run's first two steps (4e8 values of
+the sequence, about 100 barrier rounds a step); every generator's ensemble
+moments match the exactly propagated covariance of the discrete scheme within
+3 sigma."""
 import math
 
 import numpy as np
@@ -35,6 +38,26 @@ def test_hundred_million_oscillators(G, kind):
     s = G.LdSystem(r, x, v, **p)
     G.ld_init_equilibrium(s)
     picks = np.array([0, 1, 12345678, n // 2, n - 2, n - 1])
+    if kind == "lagfib":
+        # every oscillator over the first two steps, from the state the
+        # equilibrium start left: the oracle continues the sequence from the
+        # library's portable state (the last ll values, in order)
+        hd, ring = G.parse_state(G.rng_get_state(r))
+        sl, ll = G.rng_lfg_lags(hd["lag_row"])
+        g = oracle.Gen.custom_lfg(c["seed"], sl, ll,
+                                  ring=np.frombuffer(ring, dtype=np.uint32))
+        xs, vs = x.cpu().numpy(), v.cpu().numpy()
+        G.ld_run(s, 2, stats=False)
+        oracle.ld_run_f32(g, xs, vs, oracle.params(**p), 2)
+        for got, exp in ((x, xs), (v, vs)):
+            exp64 = exp.astype(np.float64)
+            rms = float(np.sqrt((exp64 * exp64).mean()))
+            err = np.abs(got.cpu().numpy().astype(np.float64) - exp64) / np.maximum(
+                np.abs(exp64), rms)
+            assert float(err.max()) <= 1e-5
+        assert G.parse_state(G.rng_get_state(r))[1] == g.ring_in_order().tobytes()
+        del xs, vs, g
+        steps -= 2
     st = G.ld_run(s, steps)
     if kind != "lagfib":
         # streams are counter-seeded: the oracle seeds just the sampled ones
