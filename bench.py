@@ -984,9 +984,7 @@ def run_sweep():
         s = G.LdSystem(r, x, torch.zeros_like(x), **PARAMS)
         G.ld_init_equilibrium(s)
         sl, ll = G.rng_lfg_lags(row)
-        ring = 1
-        while ring < 2 * ll + 2 * (ll - sl) + 16384:
-            ring <<= 1
+        ring = (2 * ll + 2 * (ll - sl) + 31) // 32 * 32
         lag_rows.append({"row": row, "sl": sl, "ll": ll, "ring_bytes": 4 * ring,
                          "portable_state_bytes": G.rng_state_bytes(r),
                          "ms_per_1000": timed(lambda: G.ld_run(s, steps, stats=False))})

@@ -158,6 +158,18 @@ int rng_set_wait_limit_ns(uint64_t ns);
  * hook off (the default).  Process-wide. */
 int gbrng_test_stall_chunk(int64_t chunk);
 
+/* Leap order k of the Lagged Fibonacci schedule (Sec. III.C, Algorithm 3, in
+ * the leap form x_p = sum_j C(k, j) x_{p - (k-j) ll - j (ll - sl)}, k + 1 lag
+ * reads per value, rounds of up to k (ll - sl) positions between grid
+ * barriers).  0 (the default) lets each launch take its own order (2); 1, 2
+ * or 4 forces that order on every later launch.  A handle's ring serves order
+ * 4 only when 4 was set before the handle was created (its ring is then
+ * 4 (2 ll - sl) words instead of 2 (2 ll - sl)); on other handles an order-4
+ * setting runs order 2.  Every order yields the same sequence bit for bit:
+ * this only trades lag reads against barrier rounds.  Process-wide;
+ * GBRNG_EINVAL for other values. */
+int gbrng_set_lfg_order(int k);
+
 /* --------------------------------------------------------- Langevin dynamics */
 
 /* One system of n independent 3-D oscillators (Sec. IV): caller-owned device

@@ -53,11 +53,15 @@ struct Handle {
     int32_t* r2 = nullptr;     // [35][n]: idum, idum2, iy, iv[0..31]
     uint32_t* lcg = nullptr;   // [n] Quick and Dirty LCG words
 
-    // Lagged Fibonacci: the sequence value at position p lives in
-    // ring[p & ring_mask]; ring size R = ring_mask + 1 >= 2 ll + 2 (ll - sl).
+    // Lagged Fibonacci: the sequence value at position p (p >= -order_max ll)
+    // lives in ring[p mod ring_size]; ring_size >= order_max (ll + (ll - sl)),
+    // where order_max (2 or 4) is the highest leap order the ring serves.  The
+    // allocation holds ring_size + ring_mirror(ring_size) words: the ring,
+    // then a copy of its first ring_mirror(ring_size) slots.
     int row = -1;
     int32_t sl = 0, ll = 0;
-    uint32_t ring_mask = 0;
+    int order_max = 2;
+    uint32_t ring_size = 0;
     uint32_t* ring = nullptr;
     int64_t pos = 0;           // next position to generate
 
@@ -73,6 +77,9 @@ struct Handle {
     float* adj = nullptr;           // adjoint checkpoints and noise (history or one segment)
     size_t adj_bytes = 0;
 };
+
+// Mirrored slots after a Lagged Fibonacci ring of R slots.
+inline uint32_t ring_mirror(uint32_t R) { return R < 32768u ? R : 32768u; }
 
 // Device attributes used for launch sizing (cached per device).
 struct DevInfo {
@@ -105,6 +112,7 @@ int ld_run_pt(const ld_system* s, int64_t n_steps, ld_stats* out, cudaStream_t s
 
 // Lagged Fibonacci entry points (lfg.cu)
 int lfg_seed(Handle* h, cudaStream_t st);
+int lfg_order_for_new_handle();   // highest leap order a new handle's ring serves
 int lfg_fill(Handle* h, void* dst, int64_t n, int mode, cudaStream_t st);  // mode 0 u32, 1 uniform, 2 normal
 int lfg_ld(const ld_system* s, int64_t n_steps, int init, ld_stats* out, cudaStream_t st);
 

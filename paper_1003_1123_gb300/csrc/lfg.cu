@@ -1,33 +1,48 @@
 // Additive Lagged Fibonacci generator shared by all threads (Algorithm 3):
 //   x_p = x_{p-ll} + x_{p-D}  mod 2^32,   D = ll - sl.
 //
-// Leap.  Applying the recurrence to both terms gives, for p >= ll,
-//   x_p = x_{p-2ll} + 2 x_{p-ll-D} + x_{p-2D}  mod 2^32,
-// the same value with the nearest dependency twice as far back (2D instead of
-// D).  Positions below ll (the first ll values after seeding) use the
-// recurrence itself.
+// Leap.  Applying the recurrence k times (in shift-operator form,
+// x = (E^{-ll} + E^{-D})^k x) gives
+//   x_p = sum_{j=0..k} C(k, j) x_{p - (k-j) ll - j D}  mod 2^32,
+// the same value with its nearest dependency k D back instead of D.  It holds
+// at p whenever the recurrence holds at every index from p - (k-1) ll on.  The
+// seeds x_{-ll..-1} are extended backwards with the recurrence run in reverse,
+// x_q = x_{q+ll} - x_{q+sl}, down to x_{-K ll} (K = the ring's highest order,
+// 2, or 4 when that order was set before the handle was created); the
+// recurrence then holds from -(K-1) ll on, so every position p >= 0 may use
+// any order k <= K.  A launch uses one order k in {1, 2, 4}: k + 1 lag reads
+// per value.  Order 2 is the default everywhere: order 4 halves the barrier
+// rounds but its two extra lag reads cost more than the barriers they save
+// (measured on every launch kind).
 //
-// Rounds.  A launch walks its positions in rounds of W consecutive positions.
-// Every position of a round depends only on earlier rounds when W <= D (a
-// round that starts below ll) or W <= 2D (from ll on), so a round is computed
-// by the whole persistent grid at once, and rounds are separated by a grid
-// barrier.  Position p lives in ring[p & mask], a power-of-two ring of
-// R >= 2 ll + 2D + 16384 words; W <= R - 2 ll keeps every overwritten value
-// (position p - R) out of reach of the round's readers.  For the fused
-// Langevin step a round also holds at most one step (W <= 4N), so each
-// oscillator is updated at most once per round.  This is the paper's
+// Ring.  Position p lives in slot p mod R of a ring of R >= K (ll + D) words
+// (rounded up to 32 words: 40.3 MB for the last Table I row at K = 2).  Slot
+// arithmetic is 32-bit: an offset below R is added with one conditional
+// subtraction of R.  The first M = min(32768, R) slots are mirrored after the
+// ring (words R .. R + M - 1; every store to a slot below M also stores its
+// mirror), so any window of at most M positions starting at slot s < R is the
+// contiguous range [s, s + M) of the allocation: lag windows never wrap, and
+// only the stores of a region that reaches the seam need per-value slots.
+//
+// Rounds.  A launch walks its positions in rounds of W consecutive positions
+// with W <= k D, so no position of a round reads another, and W <= R - k ll,
+// so no position of a round overwrites (slot p - R) a value this or a later
+// round still reads (p - k ll at the farthest).  The persistent cooperative
+// grid computes a round at once and rounds are separated by a grid barrier.
+// For the fused Langevin step a round also holds at most one step (W <= 4N),
+// so each oscillator is updated at most once per round.  This is the paper's
 // one-step-per-launch scheme (Sec. III.C) made exact for any N: the leap turns
-// its race condition ll - sl > 4N into 2(ll - sl) >= W.
+// its race condition ll - sl > 4N into k (ll - sl) >= W.
 //
 // Within a round a warp owns blocks of 128 consecutive positions (32
-// oscillator-steps): lane l reads positions 32k + l of each lag window
+// oscillator-steps): lane l reads positions 32i + l of each lag window
 // (coalesced), the new values go back to the ring the same way, and a per-warp
 // shared-memory buffer hands lane l positions 4l..4l+3.  A block none of whose
-// windows wraps around the ring addresses each window once (32-bit slot
-// arithmetic, immediate offsets).  The grid barrier is an arrival counter
-// polled under a %globaltimer bound; a wait that runs out records
-// GBRNG_ETIMEOUT and every CTA returns.
+// windows wraps around the ring addresses each window with one pointer.  The
+// grid barrier is an arrival counter polled under a %globaltimer bound; a wait
+// that runs out records GBRNG_ETIMEOUT and every CTA returns.
 #include <algorithm>
+#include <atomic>
 
 #include "device.cuh"
 #include "internal.cuh"
@@ -36,22 +51,24 @@ namespace gb {
 
 enum { LFG_U32 = 0, LFG_UNIFORM = 1, LFG_NORMAL = 2, LFG_LD = 3, LFG_LD_INIT = 4 };
 
-constexpr int kLfgThreads = 256;   // three CTAs per SM (80 registers): 24 warps to hide HBM latency;
+constexpr int kLfgThreads = 256;   // three CTAs per SM: 24 warps to hide HBM latency;
                                    // two or four CTAs per SM: fills 5-6% slower
 constexpr int kLfgWarps = kLfgThreads / 32;
 constexpr int kLfgDepth = 2;     // blocks per warp with lag loads in flight
+constexpr int kMaxOrder = 4;
 
 struct LfgArgs {
-    uint32_t* ring;
-    uint32_t mask;
-    uint32_t oA, oB, oC;   // slot offsets of the leap lags: -2ll, -ll-D, -2D (mod 2^32)
+    uint32_t* ring;                  // R + M words: the ring, then the mirror of its first M slots
+    uint32_t R;                      // ring slots
+    uint32_t M;                      // mirrored slots
+    uint32_t off[kMaxOrder + 1];     // slot offset of leap term j: -((k-j) ll + j D) mod R
+    uint32_t base_slot;              // slot of position `base`
     int32_t ll, sl;
     int64_t base;          // first position of this launch
     int64_t n_pos;         // positions of this launch
     int64_t N;             // LD: oscillators
     int64_t n_steps;       // LD: steps (init: 2)
-    int64_t w_base;        // round width (positions) while the round starts below ll
-    int64_t w_leap;        // round width from ll on
+    int64_t w;             // round width (positions)
     void* out;
     float* x;
     float* v;
@@ -63,6 +80,20 @@ struct LfgArgs {
     double* partials;      // [G][4]
     int stall_cta;         // test hook: this CTA never arrives (-1: none)
 };
+
+// s + o mod R for s, o < R (R < 2^31).
+__host__ __device__ __forceinline__ uint32_t slot_add(uint32_t s, uint32_t o, uint32_t R)
+{
+    const uint32_t r = s + o;
+    return r >= R ? r - R : r;
+}
+
+// Slot of position p (p >= -order_max ll).
+static uint32_t slot_of(int64_t p, uint32_t R)
+{
+    const int64_t r = p % (int64_t)R;
+    return (uint32_t)(r < 0 ? r + R : r);
+}
 
 // Grid barrier: after the CTA's threads meet, thread 0 adds one arrival with
 // release semantics (publishing the CTA's writes) and polls the counter
@@ -101,84 +132,89 @@ __device__ bool grid_barrier(const LfgArgs& a, uint64_t target, bool arrive_here
     return s_ok != 0;
 }
 
-// The lags of one position: value = A + 2 B + C with (A, B, C) =
-// (x_{q-2ll}, x_{q-ll-D}, x_{q-2D}) from ll on (leap) and
-// (x_{q-ll}, 0, x_{q-D}) below ll (the recurrence itself).
+// The k + 1 lag terms of one position, t[j] = x_{q - (k-j) ll - j D}, and the
+// value they give: sum_j C(k, j) t[j] mod 2^32.
+template <int K>
 struct Lags {
-    uint32_t A, B, C;
-    __device__ __forceinline__ uint32_t value() const { return A + 2u * B + C; }
+    uint32_t t[K + 1];
+    __device__ __forceinline__ uint32_t value() const
+    {
+        if (K == 1) return t[0] + t[1];
+        if (K == 2) return t[0] + 2u * t[1] + t[2];
+        return t[0] + t[4] + 4u * (t[1] + t[3]) + 6u * t[2];   // K == 4
+    }
 };
 
-__device__ __forceinline__ Lags load_lags(const LfgArgs& a, int64_t q)
+// Store val to slot e of the allocation (e < R + M), keeping the mirror: the
+// primary slot of a mirror word and the mirror of a primary slot below M.
+__device__ __forceinline__ void ring_store(const LfgArgs& a, uint32_t e, uint32_t val)
 {
-    const int64_t ll = a.ll, D = (int64_t)a.ll - a.sl;
-    const bool leap = q >= ll;
-    const uint32_t* r = a.ring;
-    Lags g;
-    g.A = __ldcg(r + ((uint64_t)(q - (leap ? 2 * ll : ll)) & a.mask));
-    g.B = leap ? __ldcg(r + ((uint64_t)(q - ll - D) & a.mask)) : 0u;
-    g.C = __ldcg(r + ((uint64_t)(q - (leap ? 2 * D : D)) & a.mask));
+    __stcg(a.ring + e, val);
+    if (e >= a.R)
+        __stcg(a.ring + (e - a.R), val);
+    else if (e < a.M)
+        __stcg(a.ring + (e + a.R), val);
+}
+
+// A region of `span` slots from s needs no mirror bookkeeping when it lies in
+// [M, R).
+__device__ __forceinline__ bool plain_stores(const LfgArgs& a, uint32_t s, uint32_t span)
+{
+    return s >= a.M && s <= a.R - span;
+}
+
+// The lags of the position in slot s.
+template <int K>
+__device__ __forceinline__ Lags<K> load_lags(const LfgArgs& a, uint32_t s)
+{
+    Lags<K> g;
+#pragma unroll
+    for (int j = 0; j <= K; ++j) g.t[j] = __ldcg(a.ring + slot_add(s, a.off[j], a.R));
     return g;
 }
 
-// A block of 128 positions from q0 is "fast" when it is whole, lies at or
-// above ll and none of its lag windows nor its own slots wraps around the ring.
-__device__ __forceinline__ bool block_fast(const LfgArgs& a, int64_t q0, int nval)
-{
-    const uint32_t s = (uint32_t)q0, lim = a.mask - 127u;
-    return nval == 128 && q0 >= a.ll && (s & a.mask) <= lim && ((s + a.oA) & a.mask) <= lim &&
-           ((s + a.oB) & a.mask) <= lim && ((s + a.oC) & a.mask) <= lim;
-}
-
-// Issue the lag loads of lane's positions q0 + 32k + lane (k < 4, < nval).
-__device__ __forceinline__ void block_load(const LfgArgs& a, int64_t q0, int nval, bool fast,
-                                           Lags (&g)[4])
+// Issue the lag loads of lane's positions (slots s0 + 32i + lane, i < 4): each
+// window is contiguous through the mirror (128 <= M), and the values past a
+// partial block's end are read but not used.
+template <int K>
+__device__ __forceinline__ void block_load(const LfgArgs& a, uint32_t s0, Lags<K> (&g)[4])
 {
     const int lane = threadIdx.x & 31;
-    if (fast) {
-        const uint32_t s = (uint32_t)q0 + lane;
-        const uint32_t* pA = a.ring + ((s + a.oA) & a.mask);
-        const uint32_t* pB = a.ring + ((s + a.oB) & a.mask);
-        const uint32_t* pC = a.ring + ((s + a.oC) & a.mask);
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            g[k].A = __ldcg(pA + 32 * k);
-            g[k].B = __ldcg(pB + 32 * k);
-            g[k].C = __ldcg(pC + 32 * k);
-        }
-    } else {
+    for (int j = 0; j <= K; ++j) {
+        const uint32_t* p = a.ring + slot_add(s0, a.off[j], a.R) + lane;
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            if (32 * k + lane < nval) g[k] = load_lags(a, q0 + 32 * k + lane);
+        for (int i = 0; i < 4; ++i) g[i].t[j] = __ldcg(p + 32 * i);
     }
 }
 
-// Store lane's values of positions q0 + 32k + lane to the ring and to the
-// warp's buffer (buf[32k + lane]).
-__device__ __forceinline__ void block_store(const LfgArgs& a, int64_t q0, int nval, bool fast,
-                                            const Lags (&g)[4], uint32_t* buf)
+// Store lane's values of slots s0 + 32i + lane (those below nval) to the ring
+// and all four to the warp's buffer (buf[32i + lane]).
+template <int K>
+__device__ __forceinline__ void block_store(const LfgArgs& a, uint32_t s0, int nval,
+                                            const Lags<K> (&g)[4], uint32_t* buf)
 {
     const int lane = threadIdx.x & 31;
-    if (fast) {
-        uint32_t* p = a.ring + (((uint32_t)q0 + lane) & a.mask);
+    if (nval == 128 && plain_stores(a, s0, 128)) {
+        uint32_t* p = a.ring + s0 + lane;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const uint32_t val = g[k].value();
-            __stcg(p + 32 * k, val);
-            buf[32 * k + lane] = val;
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t val = g[i].value();
+            __stcg(p + 32 * i, val);
+            buf[32 * i + lane] = val;
         }
     } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int i = 32 * k + lane;
-            const uint32_t val = g[k].value();
-            if (i < nval) __stcg(a.ring + ((uint64_t)(q0 + i) & a.mask), val);
-            buf[i] = val;
+        for (int i = 0; i < 4; ++i) {
+            const int e = 32 * i + lane;
+            const uint32_t val = g[i].value();
+            if (e < nval) ring_store(a, s0 + e, val);
+            buf[e] = val;
         }
     }
 }
 
-// Lane l's four consecutive values (positions q0 + 4l .. q0 + 4l + 3).
+// Lane l's four consecutive values (positions 4l .. 4l + 3 of the block).
 __device__ __forceinline__ uint4 block_transpose(const uint32_t* buf)
 {
     __syncwarp();
@@ -187,26 +223,27 @@ __device__ __forceinline__ uint4 block_transpose(const uint32_t* buf)
     return w;
 }
 
-// Walk this warp's blocks b = first, first + step, ... < nblk of a region
-// starting at q_first (positions q_first + 128 b ..), with the lag loads of
-// the next kLfgDepth - 1 blocks in flight while one block is consumed.
-// Positions of one round never read each other, so the early loads are exact.
+// Walk this warp's blocks b = first, first + step, ... < nblk of a region of
+// n_region positions whose first position lives in slot s_first (block b
+// starts 128 b later, 128 b < n_region <= R), with the lag loads of the next
+// kLfgDepth - 1 blocks in flight while one is consumed.  Positions of one
+// round never read each other, so the early loads are exact.
 // consume(b, nval, w) receives lane's four values after they are stored.
-template <class F>
-__device__ __forceinline__ void walk_blocks(const LfgArgs& a, int64_t q_first, int64_t n_region,
+template <int K, class F>
+__device__ __forceinline__ void walk_blocks(const LfgArgs& a, uint32_t s_first, int64_t n_region,
                                             int64_t first, int64_t step, uint32_t* buf, F&& consume)
 {
     const int64_t nblk = (n_region + 127) >> 7;
-    Lags pipe[kLfgDepth][4];
-    bool fast[kLfgDepth];
+    Lags<K> pipe[kLfgDepth][4];
     int nv[kLfgDepth];
+    uint32_t sl[kLfgDepth];
 #pragma unroll
     for (int d = 0; d < kLfgDepth - 1; ++d) {
         const int64_t b = first + d * step;
         if (b < nblk) {
             nv[d] = (int)min((int64_t)128, n_region - 128 * b);
-            fast[d] = block_fast(a, q_first + 128 * b, nv[d]);
-            block_load(a, q_first + 128 * b, nv[d], fast[d], pipe[d]);
+            sl[d] = slot_add(s_first, (uint32_t)(128 * b), a.R);
+            block_load<K>(a, sl[d], pipe[d]);
         }
     }
     for (int64_t b = first; b < nblk; b += step) {
@@ -214,17 +251,17 @@ __device__ __forceinline__ void walk_blocks(const LfgArgs& a, int64_t q_first, i
         if (bn < nblk) {
             constexpr int L = kLfgDepth - 1;
             nv[L] = (int)min((int64_t)128, n_region - 128 * bn);
-            fast[L] = block_fast(a, q_first + 128 * bn, nv[L]);
-            block_load(a, q_first + 128 * bn, nv[L], fast[L], pipe[L]);
+            sl[L] = slot_add(s_first, (uint32_t)(128 * bn), a.R);
+            block_load<K>(a, sl[L], pipe[L]);
         }
-        block_store(a, q_first + 128 * b, nv[0], fast[0], pipe[0], buf);
+        block_store<K>(a, sl[0], nv[0], pipe[0], buf);
         consume(b, nv[0], block_transpose(buf));
 #pragma unroll
         for (int d = 0; d < kLfgDepth - 1; ++d) {
-            fast[d] = fast[d + 1];
             nv[d] = nv[d + 1];
+            sl[d] = sl[d + 1];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) pipe[d][k] = pipe[d + 1][k];
+            for (int i = 0; i < 4; ++i) pipe[d][i] = pipe[d + 1][i];
         }
     }
 }
@@ -256,7 +293,7 @@ __device__ __forceinline__ void em_update(const LdCoef& c, float Ki, float g0, f
     }
 }
 
-template <int MODE>
+template <int MODE, int K>
 __global__ void __launch_bounds__(kLfgThreads, 3) lfg_kernel(LfgArgs a)
 {
     __shared__ __align__(16) uint32_t bufs[kLfgWarps][128];
@@ -269,40 +306,40 @@ __global__ void __launch_bounds__(kLfgThreads, 3) lfg_kernel(LfgArgs a)
     Kahan e;
     double acc[3] = {0, 0, 0};
     uint64_t round = 0;
+    uint32_t s_round = a.base_slot;   // slot of position base + U
     for (int64_t U = 0; U < a.n_pos; ++round) {
         // rounds: whole oscillator-steps for the fused step (U, widths are multiples of 4)
-        const int64_t wpos = a.base + U >= a.ll ? a.w_leap : a.w_base;
-        const int64_t U1 = min(a.n_pos, U + wpos);
+        const int64_t U1 = min(a.n_pos, U + a.w);
         if (!LD) {
-            walk_blocks(a, a.base + U, U1 - U, gwarp, nwarps, bufs[warp],
-                        [&](int64_t b, int nval, uint4 w) {
-                            const int64_t u0 = U + 128 * b;   // launch offset of the block
-                            if (MODE == LFG_NORMAL) {
-                                // positions u0 + 4l .. + 3: pairs (2e, 2e + 1); nval is even
-                                const int i = 4 * lane;
-                                float2 o;
-                                if (i < nval) {
-                                    box_muller_u32(w.x, w.y, o.x, o.y);
-                                    __stcs((float2*)((float*)a.out + u0 + i), o);
-                                }
-                                if (i + 2 < nval) {
-                                    box_muller_u32(w.z, w.w, o.x, o.y);
-                                    __stcs((float2*)((float*)a.out + u0 + i + 2), o);
-                                }
-                            } else {
-                                const uint32_t* bv = bufs[warp];
+            walk_blocks<K>(a, s_round, U1 - U, gwarp, nwarps, bufs[warp],
+                           [&](int64_t b, int nval, uint4 w) {
+                               const int64_t u0 = U + 128 * b;   // launch offset of the block
+                               if (MODE == LFG_NORMAL) {
+                                   // positions u0 + 4l .. + 3: pairs (2e, 2e + 1); nval is even
+                                   const int i = 4 * lane;
+                                   float2 o;
+                                   if (i < nval) {
+                                       box_muller_u32(w.x, w.y, o.x, o.y);
+                                       __stcs((float2*)((float*)a.out + u0 + i), o);
+                                   }
+                                   if (i + 2 < nval) {
+                                       box_muller_u32(w.z, w.w, o.x, o.y);
+                                       __stcs((float2*)((float*)a.out + u0 + i + 2), o);
+                                   }
+                               } else {
+                                   const uint32_t* bv = bufs[warp];
 #pragma unroll
-                                for (int k = 0; k < 4; ++k) {
-                                    const int i = 32 * k + lane;
-                                    if (i < nval) {
-                                        if (MODE == LFG_U32)
-                                            __stcs((uint32_t*)a.out + u0 + i, bv[i]);
-                                        else
-                                            __stcs((float*)a.out + u0 + i, u01_from_u32(bv[i]));
-                                    }
-                                }
-                            }
-                        });
+                                   for (int k = 0; k < 4; ++k) {
+                                       const int i = 32 * k + lane;
+                                       if (i < nval) {
+                                           if (MODE == LFG_U32)
+                                               __stcs((uint32_t*)a.out + u0 + i, bv[i]);
+                                           else
+                                               __stcs((float*)a.out + u0 + i, u01_from_u32(bv[i]));
+                                       }
+                                   }
+                               }
+                           });
         } else {
             // oscillator-step u = (U + 128 b) / 4 + lane; the round spans at most two steps
             const int64_t t0 = U / (4 * a.N), u_next = (t0 + 1) * a.N;
@@ -325,38 +362,39 @@ __global__ void __launch_bounds__(kLfgThreads, 3) lfg_kernel(LfgArgs a)
                     }
                 }
             }
-            walk_blocks(a, a.base + U, U1 - U, gwarp, nwarps, bufs[warp],
-                        [&](int64_t b, int nval, uint4 w) {
-                            if (4 * lane >= nval) return;
-                            const int64_t u = (U >> 2) + 32 * b + lane;
-                            const int64_t t = t0 + (u >= u_next ? 1 : 0);
-                            const int64_t j = u - t * a.N;
-                            float g0, g1, g2;
-                            normals3(w, g0, g1, g2);
-                            const float Ki = a.Kper ? __ldcg(a.Kper + j) : a.c.K;
-                            float* xp = a.x + 3 * j;
-                            float* vp = a.v + 3 * j;
-                            if (MODE == LFG_LD_INIT) {
-                                if (t == 0) {
-                                    const float sx = __fsqrt_rn(__fdiv_rn(a.c.kT, Ki));
-                                    __stcg(xp, __fmul_rn(sx, g0));
-                                    __stcg(xp + 1, __fmul_rn(sx, g1));
-                                    __stcg(xp + 2, __fmul_rn(sx, g2));
-                                } else {
-                                    __stcg(vp, __fmul_rn(a.c.sv, g0));
-                                    __stcg(vp + 1, __fmul_rn(a.c.sv, g1));
-                                    __stcg(vp + 2, __fmul_rn(a.c.sv, g2));
-                                }
-                                return;
-                            }
-                            float x0 = __ldca(xp), x1 = __ldca(xp + 1), x2 = __ldca(xp + 2);
-                            float v0 = __ldca(vp), v1 = __ldca(vp + 1), v2 = __ldca(vp + 2);
-                            em_update(a.c, Ki, g0, g1, g2, x0, x1, x2, v0, v1, v2,
-                                      t == a.n_steps - 1, e, acc);
-                            __stcg(xp, x0), __stcg(xp + 1, x1), __stcg(xp + 2, x2);
-                            __stcg(vp, v0), __stcg(vp + 1, v1), __stcg(vp + 2, v2);
-                        });
+            walk_blocks<K>(a, s_round, U1 - U, gwarp, nwarps, bufs[warp],
+                           [&](int64_t b, int nval, uint4 w) {
+                               if (4 * lane >= nval) return;
+                               const int64_t u = (U >> 2) + 32 * b + lane;
+                               const int64_t t = t0 + (u >= u_next ? 1 : 0);
+                               const int64_t j = u - t * a.N;
+                               float g0, g1, g2;
+                               normals3(w, g0, g1, g2);
+                               const float Ki = a.Kper ? __ldcg(a.Kper + j) : a.c.K;
+                               float* xp = a.x + 3 * j;
+                               float* vp = a.v + 3 * j;
+                               if (MODE == LFG_LD_INIT) {
+                                   if (t == 0) {
+                                       const float sx = __fsqrt_rn(__fdiv_rn(a.c.kT, Ki));
+                                       __stcg(xp, __fmul_rn(sx, g0));
+                                       __stcg(xp + 1, __fmul_rn(sx, g1));
+                                       __stcg(xp + 2, __fmul_rn(sx, g2));
+                                   } else {
+                                       __stcg(vp, __fmul_rn(a.c.sv, g0));
+                                       __stcg(vp + 1, __fmul_rn(a.c.sv, g1));
+                                       __stcg(vp + 2, __fmul_rn(a.c.sv, g2));
+                                   }
+                                   return;
+                               }
+                               float x0 = __ldca(xp), x1 = __ldca(xp + 1), x2 = __ldca(xp + 2);
+                               float v0 = __ldca(vp), v1 = __ldca(vp + 1), v2 = __ldca(vp + 2);
+                               em_update(a.c, Ki, g0, g1, g2, x0, x1, x2, v0, v1, v2,
+                                         t == a.n_steps - 1, e, acc);
+                               __stcg(xp, x0), __stcg(xp + 1, x1), __stcg(xp + 2, x2);
+                               __stcg(vp, v0), __stcg(vp + 1, v1), __stcg(vp + 2, v2);
+                           });
         }
+        s_round = slot_add(s_round, (uint32_t)(U1 - U), a.R);
         U = U1;
         if (U < a.n_pos && !grid_barrier(a, (uint64_t)gridDim.x * (round + 1), arrive_here)) return;
     }
@@ -370,19 +408,24 @@ __global__ void __launch_bounds__(kLfgThreads, 3) lfg_kernel(LfgArgs a)
 }
 
 // ------------------------------------------------- fused step, resident state
-// When every step of the launch fits an all-leap round (4N <= the round width
-// and the launch starts at or above ll), CTA c owns the oscillators
+// When every step of the launch fits a round (4N <= the round width) and the
+// CTAs' shares of x and v fit in shared memory, CTA c owns the oscillators
 // [c n_c, c n_c + n_c) for the whole launch and keeps their x and v in shared
 // memory: a step's global traffic is then the ring alone.  A round holds
 // floor(width / 4N) steps, since an oscillator's consecutive steps stay with
 // one lane and only the ring is shared.  A step's positions for the CTA are
-// one contiguous region; when none of its windows wraps around the ring (all
-// but about one step in R / 4N), each lane addresses the region with one
-// pointer per window and the blocks are walked two at a time, the loads of one
-// in flight while the other is consumed.
-constexpr int kResThreads = 512;
+// one contiguous region of at most M slots, so each lane addresses each of its
+// windows with one pointer (through the mirror), and the blocks are walked two
+// at a time, the loads of one in flight while the other is consumed.  (Before
+// the mirror, a region whose window wrapped took a slower per-block path;
+// with 152 CTAs about one did so every step and held up the barrier: 13.2
+// against 11.6 us per step at 1e6 oscillators on a 40 MB ring.)
+// 640 threads (20 warps, up to 102 registers): 11.6 us per step at 1e6
+// oscillators against 12.2 with 512 and 11.7 with 768 (same GB300, same ring).
+constexpr int kResThreads = 640;
 constexpr int kResWarps = kResThreads / 32;
 
+template <int K>
 __global__ void __launch_bounds__(kResThreads, 1) lfg_resident_kernel(LfgArgs a, int64_t n_c)
 {
     extern __shared__ __align__(16) float res_sm[];
@@ -406,7 +449,10 @@ __global__ void __launch_bounds__(kResThreads, 1) lfg_resident_kernel(LfgArgs a,
     // kr steps per round: their 4 N kr positions read only earlier rounds, and
     // each oscillator's steps stay with one lane, so no barrier is needed
     // inside a round
-    const int64_t kr = max((int64_t)1, a.w_leap / (4 * a.N));
+    const int64_t kr = max((int64_t)1, a.w / (4 * a.N));
+    const uint32_t step_slots = (uint32_t)(4 * a.N);   // 4N <= w < R
+    // slot of this CTA's first position in step t (4 j0 <= 4N < R)
+    uint32_t sP = slot_add(a.base_slot, (uint32_t)(4 * min(j0, a.N)), a.R);
     for (int64_t t = 0; t < a.n_steps; ++t) {
         const bool last = t == a.n_steps - 1;
         // oscillator jj of this CTA from its four values w
@@ -422,58 +468,54 @@ __global__ void __launch_bounds__(kResThreads, 1) lfg_resident_kernel(LfgArgs a,
             xp[0] = x0, xp[1] = x1, xp[2] = x2;
             vp[0] = v0, vp[1] = v1, vp[2] = v2;
         };
-        const int64_t P = a.base + 4 * (t * a.N + j0);
-        const uint32_t P32 = (uint32_t)P;
-        const uint32_t span = 128u * (uint32_t)nblk;   // whole blocks, loads may read past npos
-        const uint32_t sA = (P32 + a.oA) & a.mask, sB = (P32 + a.oB) & a.mask;
-        const uint32_t sC = (P32 + a.oC) & a.mask, sS = P32 & a.mask;
-        const bool fast = span <= a.mask && sA <= a.mask + 1 - span && sB <= a.mask + 1 - span &&
-                          sC <= a.mask + 1 - span && sS <= a.mask + 1 - span;
-        if (fast) {
-            const uint32_t* pA = a.ring + sA + lane;
-            const uint32_t* pB = a.ring + sB + lane;
-            const uint32_t* pC = a.ring + sC + lane;
-            uint32_t* pS = a.ring + sS + lane;
-            auto load = [&](int b, Lags(&g)[4]) {
-                const int o = 128 * b;
+        // every window of the step's region is contiguous through the mirror
+        // (whole blocks: loads may read up to 127 values past npos, span <= M)
+        const uint32_t span = 128u * (uint32_t)nblk;
+        const bool plain = plain_stores(a, sP, span);
+        const uint32_t* pw[K + 1];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    g[k].A = __ldcg(pA + o + 32 * k);
-                    g[k].B = __ldcg(pB + o + 32 * k);
-                    g[k].C = __ldcg(pC + o + 32 * k);
-                }
-            };
-            auto consume = [&](int b, const Lags(&g)[4]) {
-                const int o = 128 * b;
-                const bool whole = o + 128 <= npos;
+        for (int j = 0; j <= K; ++j) pw[j] = a.ring + slot_add(sP, a.off[j], a.R) + lane;
+        uint32_t* pS = a.ring + sP + lane;
+        auto load = [&](int b, Lags<K>(&g)[4]) {
+            const int o = 128 * b;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t val = g[k].value();
-                    if (whole || o + 32 * k + lane < npos) __stcg(pS + o + 32 * k, val);
-                    buf[32 * k + lane] = val;
+            for (int j = 0; j <= K; ++j)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) g[i].t[j] = __ldcg(pw[j] + o + 32 * i);
+        };
+        auto consume = [&](int b, const Lags<K>(&g)[4]) {
+            const int o = 128 * b;
+            const bool whole = o + 128 <= npos;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t val = g[i].value();
+                const int e = o + 32 * i + lane;
+                if (whole || e < npos) {
+                    if (plain)
+                        __stcg(pS + o + 32 * i, val);
+                    else
+                        ring_store(a, sP + e, val);
                 }
-                const uint4 w = block_transpose(buf);
-                const int jj = 32 * b + lane;
-                if (jj < nc) osc(jj, w);
-            };
-            Lags g0[4], g1[4];
-            int b = warp;
-            if (b < nblk) load(b, g0);
-            while (b < nblk) {
-                const int b1 = b + kResWarps;
-                if (b1 < nblk) load(b1, g1);
-                consume(b, g0);
-                if (b1 >= nblk) break;
-                const int b2 = b1 + kResWarps;
-                if (b2 < nblk) load(b2, g0);
-                consume(b1, g1);
-                b = b2;
+                buf[32 * i + lane] = val;
             }
-        } else {
-            walk_blocks(a, P, npos, warp, kResWarps, buf, [&](int64_t b, int nval, uint4 w) {
-                if (4 * lane < nval) osc(32 * (int)b + lane, w);
-            });
+            const uint4 w = block_transpose(buf);
+            const int jj = 32 * b + lane;
+            if (jj < nc) osc(jj, w);
+        };
+        Lags<K> g0[4], g1[4];
+        int b = warp;
+        if (b < nblk) load(b, g0);
+        while (b < nblk) {
+            const int b1 = b + kResWarps;
+            if (b1 < nblk) load(b1, g1);
+            consume(b, g0);
+            if (b1 >= nblk) break;
+            const int b2 = b1 + kResWarps;
+            if (b2 < nblk) load(b2, g0);
+            consume(b1, g1);
+            b = b2;
         }
+        sP = slot_add(sP, step_slots, a.R);
         if (!last && (t + 1) % kr == 0 &&
             !grid_barrier(a, (uint64_t)gridDim.x * (uint64_t)((t + 1) / kr), arrive_here))
             return;
@@ -494,20 +536,22 @@ __global__ void __launch_bounds__(kResThreads, 1) lfg_resident_kernel(LfgArgs a,
 
 // ----------------------------------------------------------- paper form
 // One launch per step (Algorithm 3 with Sec. III.C's one-step-per-launch
-// scheme): thread j computes positions P + 4j .. P + 4j + 3 from the ring,
-// stores them, and takes oscillator j's step with x, v and its energy sum in
-// global memory.  The launch boundary is the only synchronisation, so every
-// position of the step must be dependency-free (checked on the host).
-__global__ void __launch_bounds__(256) lfg_step_kernel(LfgArgs a, int64_t P, float2* eacc)
+// scheme): thread j computes positions P + 4j .. P + 4j + 3 (slots from sP)
+// from the ring, stores them, and takes oscillator j's step with x, v and its
+// energy sum in global memory.  The launch boundary is the only
+// synchronisation, so every position of the step must be dependency-free
+// (checked on the host).
+template <int K>
+__global__ void __launch_bounds__(256) lfg_step_kernel(LfgArgs a, uint32_t sP, float2* eacc)
 {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= a.N) return;
-    const int64_t q = P + 4 * j;
+    const uint32_t s = slot_add(sP, (uint32_t)(4 * j), a.R);   // 4j < 4N < R
     uint32_t w[4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) w[r] = load_lags(a, q + r).value();
+    for (int r = 0; r < 4; ++r) w[r] = load_lags<K>(a, slot_add(s, r, a.R)).value();
 #pragma unroll
-    for (int r = 0; r < 4; ++r) a.ring[(uint64_t)(q + r) & a.mask] = w[r];
+    for (int r = 0; r < 4; ++r) ring_store(a, slot_add(s, r, a.R), w[r]);
     float g0, g1, g2;
     box_muller_u32(w[0], w[1], g0, g1);
     g2 = box_muller_cos_u32(w[2], w[3]);
@@ -535,6 +579,7 @@ __global__ void __launch_bounds__(256) lfg_step_kernel(LfgArgs a, int64_t P, flo
 // computed by the cooperative grid and closed by the grid barrier; R lives in
 // global memory, R(0) in the handle's scratch.  Records before a step sum each
 // block's particles (R and R R(0) are read by the thread that wrote them).
+template <int K>
 __global__ void __launch_bounds__(256) lfg_ou_kernel(LfgArgs a, OuCoef c, float* R, const float* R0,
                                                      int64_t every, double* partials)
 {
@@ -542,6 +587,8 @@ __global__ void __launch_bounds__(256) lfg_ou_kernel(LfgArgs a, OuCoef c, float*
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const bool arrive_here = (int)blockIdx.x != a.stall_cta;
+    const uint32_t step_slots = (uint32_t)(2 * a.N);   // 2N <= w < ring size
+    uint32_t sP = a.base_slot;                          // slot of the step's first position
     int64_t rec = 0, next_rec = 0;
     for (int64_t t = 0;; ++t) {
         if (partials && t == next_rec) {
@@ -560,70 +607,105 @@ __global__ void __launch_bounds__(256) lfg_ou_kernel(LfgArgs a, OuCoef c, float*
             ++rec;
         }
         if (t == a.n_steps) break;
-        const int64_t P = a.base + 2 * a.N * t;
         for (int64_t j = gt; j < a.N; j += stride) {
-            const int64_t q = P + 2 * j;
-            const uint32_t w0 = load_lags(a, q).value(), w1 = load_lags(a, q + 1).value();
-            __stcg(a.ring + ((uint64_t)q & a.mask), w0);
-            __stcg(a.ring + ((uint64_t)(q + 1) & a.mask), w1);
+            const uint32_t s0 = slot_add(sP, (uint32_t)(2 * j), a.R), s1 = slot_add(s0, 1u, a.R);
+            const uint32_t w0 = load_lags<K>(a, s0).value(), w1 = load_lags<K>(a, s1).value();
+            ring_store(a, s0, w0);
+            ring_store(a, s1, w1);
             const float g = box_muller_cos_u32(w0, w1);
             R[j] = __fmaf_rn(c.cs, g, __fmaf_rn(-c.c1, R[j], R[j]));
         }
+        sP = slot_add(sP, step_slots, a.R);
         if (t + 1 < a.n_steps &&
             !grid_barrier(a, (uint64_t)gridDim.x * (uint64_t)(t + 1), arrive_here))
             return;
     }
 }
 
-// Seeds: ring word for position w - ll (w = 0..ll-1) is the low half of
-// SplitMix64 at counter w; x_{-ll} is forced odd.
-__global__ void lfg_seed_kernel(uint64_t seed, int32_t ll, uint32_t mask, uint32_t* ring)
+// Seeds: the value at position w - ll (w = 0..ll-1) is the low half of
+// SplitMix64 at counter w, and x_{-ll} is forced odd.  Positions -K ll <= q <
+// 0 live in slot q + R.
+__global__ void lfg_seed_kernel(uint64_t seed, int32_t ll, LfgArgs a)
 {
     const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (w >= ll) return;
     uint32_t v = (uint32_t)splitmix64_at(seed, (uint64_t)w);
     if (w == 0) v |= 1u;
-    ring[(uint64_t)(w - ll) & mask] = v;
+    ring_store(a, a.R - (uint32_t)ll + (uint32_t)w, v);
 }
+
+// The recurrence run backwards, x_q = x_{q+ll} - x_{q+sl}, for q in
+// [q_hi - count, q_hi): every read lies at q_hi or above (count <= sl).
+__global__ void lfg_extend_kernel(LfgArgs a, int64_t q_hi, int64_t count)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const int64_t q = q_hi - count + i;
+    const uint32_t R = a.R;
+    ring_store(a, (uint32_t)(q + R),
+               a.ring[(uint32_t)(q + a.ll + R)] - a.ring[(uint32_t)(q + a.sl + R)]);
+}
+
+static void set_ring(const Handle* h, LfgArgs& a, int k);
 
 int lfg_seed(Handle* h, cudaStream_t st)
 {
     h->pos = 0;
     const int T = 256;
-    lfg_seed_kernel<<<(unsigned)((h->ll + T - 1) / T), T, 0, st>>>(h->seed, h->ll, h->ring_mask,
-                                                                   h->ring);
+    LfgArgs a{};
+    set_ring(h, a, 1);
+    lfg_seed_kernel<<<(unsigned)((h->ll + T - 1) / T), T, 0, st>>>(h->seed, h->ll, a);
+    GB_CUDA(cudaGetLastError());
+    // x_{-K ll} .. x_{-ll-1}, in rounds of sl positions from -ll downwards
+    const int64_t lo = -(int64_t)h->order_max * h->ll;
+    for (int64_t q_hi = -(int64_t)h->ll; q_hi > lo;) {
+        const int64_t cnt = std::min<int64_t>(h->sl, q_hi - lo);
+        lfg_extend_kernel<<<(unsigned)((cnt + T - 1) / T), T, 0, st>>>(a, q_hi, cnt);
+        q_hi -= cnt;
+    }
     GB_CUDA(cudaGetLastError());
     return GBRNG_OK;
 }
 
-// Round widths: W <= D (rounds starting below ll) or 2D (from ll on), W <= R - 2ll
-// (overwritten values are out of every reader's reach), and for the fused step
-// W <= 4N; even (normal pairs) and a multiple of 4 (whole oscillators).
-static void round_widths(const Handle* h, int64_t four_n, int64_t* w_base, int64_t* w_leap)
+// ------------------------------------------------------------- host side
+// Leap order of a launch: the process-wide setting, else the given default,
+// at most the highest order the handle's ring serves.
+static std::atomic<int> g_lfg_order{0};
+
+int lfg_order_for_new_handle() { return g_lfg_order.load() == 4 ? 4 : 2; }
+
+static int pick_order(const Handle* h, int dflt)
 {
-    const int64_t D = (int64_t)h->ll - h->sl, R = (int64_t)h->ring_mask + 1;
-    const int64_t cap = R - 2 * (int64_t)h->ll;
-    int64_t wb = std::min(D, cap), wl = std::min(2 * D, cap);
-    if (four_n > 0) {
-        wb = std::min(wb, four_n);
-        wl = std::min(wl, four_n);
-    }
-    *w_base = std::max<int64_t>(wb & ~(int64_t)3, 4);
-    *w_leap = std::max<int64_t>(wl & ~(int64_t)3, 4);
+    const int o = g_lfg_order.load();
+    return std::min(o ? o : dflt, h->order_max);
 }
 
-// Ring, lags and the launch's first position.
-static void set_ring(const Handle* h, LfgArgs& a)
+// Round width for order k: W <= k D (no position of a round reads another),
+// W <= R - k ll (no overwritten value is still to be read), and for the fused
+// step W <= 4N (multiple of 4: whole oscillators; even: normal pairs).
+static int64_t round_width(const Handle* h, int k, int64_t four_n)
 {
-    const int64_t ll = h->ll, D = (int64_t)h->ll - h->sl;
+    const int64_t D = (int64_t)h->ll - h->sl, R = (int64_t)h->ring_size;
+    int64_t w = std::min<int64_t>((int64_t)k * D, R - (int64_t)k * h->ll);
+    if (four_n > 0) w = std::min(w, four_n);
+    return std::max<int64_t>(w & ~(int64_t)3, 4);
+}
+
+// Ring, order-k lag offsets and the launch's first position.
+static void set_ring(const Handle* h, LfgArgs& a, int k)
+{
+    const int64_t ll = h->ll, D = (int64_t)h->ll - h->sl, R = (int64_t)h->ring_size;
     a.ring = h->ring;
-    a.mask = h->ring_mask;
-    a.oA = (uint32_t)(-2 * ll);
-    a.oB = (uint32_t)(-ll - D);
-    a.oC = (uint32_t)(-2 * D);
+    a.R = h->ring_size;
+    a.M = ring_mirror(h->ring_size);
+    for (int j = 0; j <= kMaxOrder; ++j) {
+        const int64_t back = (int64_t)(k - j) * ll + (int64_t)j * D;
+        a.off[j] = j <= k ? (uint32_t)((R - back % R) % R) : 0u;
+    }
     a.ll = h->ll;
     a.sl = h->sl;
     a.base = h->pos;
+    a.base_slot = slot_of(h->pos, h->ring_size);
 }
 
 // Barrier counter, status word, wait limit and test hook of one launch.
@@ -640,19 +722,19 @@ static int launch_common(Handle* h, LfgArgs& a, int64_t G, cudaStream_t st)
     return GBRNG_OK;
 }
 
-template <int MODE>
-static int launch(Handle* h, LfgArgs& a, cudaStream_t st, int64_t* G_out)
+template <int MODE, int K>
+static int launch_k(Handle* h, LfgArgs& a, cudaStream_t st, int64_t* G_out)
 {
     DevInfo di;
     GB_CHECK(dev_info(h->device, &di));
-    auto fn = lfg_kernel<MODE>;
+    auto fn = lfg_kernel<MODE, K>;
     int occ = 0;
     GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kLfgThreads, 0));
     if (occ < 1) return fail(GBRNG_EINVAL, "Lagged Fibonacci kernel does not fit on an SM");
     // no more CTAs than the widest round can use
     const int64_t per_cta = 128 * kLfgWarps;   // one block per warp
     int64_t G = (int64_t)di.sms * occ;
-    G = std::min<int64_t>(G, std::max<int64_t>(1, (a.w_leap + per_cta - 1) / per_cta));
+    G = std::min<int64_t>(G, std::max<int64_t>(1, (a.w + per_cta - 1) / per_cta));
     if (G < 1) G = 1;
     if (MODE == LFG_LD) GB_CHECK(ensure_partials(h, G));
     a.partials = MODE == LFG_LD ? h->partials : nullptr;
@@ -664,39 +746,53 @@ static int launch(Handle* h, LfgArgs& a, cudaStream_t st, int64_t* G_out)
     return GBRNG_OK;
 }
 
-// The resident-state kernel applies when every step of the launch is one
-// all-leap round (4N within the leap width, launch at or above ll) and one CTA
-// per SM can hold its share of x and v.
-// Returns 1 (and launches) when it applies, 0 when the caller must use the
-// general kernel, or an error.
-static int try_launch_resident(Handle* h, LfgArgs& a, cudaStream_t st, int64_t* G_out)
+template <int MODE>
+static int launch(Handle* h, LfgArgs& a, int k, cudaStream_t st, int64_t* G_out)
 {
-    const int64_t four_n = 4 * a.N;
-    if (four_n > a.w_leap || a.base < a.ll) return 0;
+    if (k == 1) return launch_k<MODE, 1>(h, a, st, G_out);
+    if (k == 2) return launch_k<MODE, 2>(h, a, st, G_out);
+    return launch_k<MODE, 4>(h, a, st, G_out);
+}
+
+// The resident-state kernel applies when every step of the launch fits one
+// round (4N within the width) and one CTA per SM can hold its share of x and
+// v.  Returns 1 (and launches) when it applies, 0 when the caller must use the
+// general kernel, or an error.
+template <int K>
+static int try_launch_resident_k(Handle* h, LfgArgs& a, cudaStream_t st, int64_t* G_out)
+{
+    a.w = round_width(h, K, 0);   // the full width: several steps a round
+    if (4 * a.N > a.w) return 0;
     DevInfo di;
     GB_CHECK(dev_info(h->device, &di));
     const int64_t G = di.sms;
     const int64_t n_c = ((a.N + G - 1) / G + 31) & ~(int64_t)31;
+    if (4 * n_c > (int64_t)a.M) return 0;   // a CTA's step region must fit the mirror
     const size_t smem = sizeof(float) * 6 * (size_t)n_c;
     const size_t static_smem = sizeof(uint32_t) * kResWarps * 128 + sizeof(double) * 128 + 64;
     if (smem + static_smem > di.smem_optin) return 0;
-    GB_CUDA(cudaFuncSetAttribute((const void*)lfg_resident_kernel,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto fn = lfg_resident_kernel<K>;
+    GB_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
     int occ = 0;
-    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lfg_resident_kernel, kResThreads,
-                                                          smem));
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kResThreads, smem));
     if (occ < 1) return 0;
     GB_CHECK(ensure_partials(h, G));
     a.partials = h->partials;
-    int64_t w_base_full = 0;
-    round_widths(h, 0, &w_base_full, &a.w_leap);   // the full leap width: several steps a round
     GB_CHECK(launch_common(h, a, G, st));
     int64_t nc_arg = n_c;
     void* args[] = {&a, &nc_arg};
-    GB_CUDA(cudaLaunchCooperativeKernel((const void*)lfg_resident_kernel, dim3((unsigned)G),
-                                        dim3(kResThreads), args, smem, st));
+    GB_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3((unsigned)G), dim3(kResThreads), args,
+                                        smem, st));
     *G_out = G;
     return 1;
+}
+
+static int try_launch_resident(Handle* h, LfgArgs& a, int k, cudaStream_t st, int64_t* G_out)
+{
+    if (k == 1) return try_launch_resident_k<1>(h, a, st, G_out);
+    if (k == 2) return try_launch_resident_k<2>(h, a, st, G_out);
+    return try_launch_resident_k<4>(h, a, st, G_out);
 }
 
 static int read_status(Handle* h, cudaStream_t st)
@@ -710,20 +806,27 @@ static int read_status(Handle* h, cudaStream_t st)
     return GBRNG_OK;
 }
 
+// Default leap order of every launch kind (order 4, where a handle's ring
+// serves it, was slower in every one: fills 2.43 -> 3.12 ms for 2^30 values,
+// the resident fused step 11.9 -> 13.4 us and the streamed one 2.04 -> 2.47 ms
+// at 1e6 and 1e8 oscillators).
+constexpr int kOrderFill = 2, kOrderLd = 2, kOrderResident = 2, kOrderStep = 2, kOrderOu = 2;
+
 int lfg_fill(Handle* h, void* dst, int64_t n, int mode, cudaStream_t st)
 {
+    const int k = pick_order(h, kOrderFill);
     LfgArgs a{};
-    set_ring(h, a);
+    set_ring(h, a, k);
     a.n_pos = n;
-    round_widths(h, 0, &a.w_base, &a.w_leap);
+    a.w = round_width(h, k, 0);
     a.out = dst;
     int64_t G = 0;
     if (mode == LFG_U32)
-        GB_CHECK(launch<LFG_U32>(h, a, st, &G));
+        GB_CHECK(launch<LFG_U32>(h, a, k, st, &G));
     else if (mode == LFG_UNIFORM)
-        GB_CHECK(launch<LFG_UNIFORM>(h, a, st, &G));
+        GB_CHECK(launch<LFG_UNIFORM>(h, a, k, st, &G));
     else
-        GB_CHECK(launch<LFG_NORMAL>(h, a, st, &G));
+        GB_CHECK(launch<LFG_NORMAL>(h, a, k, st, &G));
     GB_CHECK(read_status(h, st));
     h->pos += n;
     return GBRNG_OK;
@@ -763,22 +866,29 @@ int lfg_ld(const ld_system* s, int64_t n_steps, int init, ld_stats* out, cudaStr
         return GBRNG_OK;
     }
     LfgArgs a{};
-    set_ring(h, a);
     a.N = s->n;
     a.n_steps = init ? 2 : n_steps;
     a.n_pos = 4 * s->n * a.n_steps;
-    round_widths(h, 4 * s->n, &a.w_base, &a.w_leap);
     a.x = s->x;
     a.v = s->v;
     a.Kper = s->K_per;
     a.c = make_coef(s);
     int64_t G = 0;
-    if (init) {
-        GB_CHECK(launch<LFG_LD_INIT>(h, a, st, &G));
-    } else {
-        const int rc = try_launch_resident(h, a, st, &G);
+    int rc = 0;
+    if (!init) {
+        const int kr = pick_order(h, kOrderResident);
+        set_ring(h, a, kr);
+        rc = try_launch_resident(h, a, kr, st, &G);
         if (rc < 0) return rc;
-        if (rc == 0) GB_CHECK(launch<LFG_LD>(h, a, st, &G));
+    }
+    if (rc == 0) {
+        const int k = pick_order(h, kOrderLd);
+        set_ring(h, a, k);
+        a.w = round_width(h, k, 4 * s->n);
+        if (init)
+            GB_CHECK(launch<LFG_LD_INIT>(h, a, k, st, &G));
+        else
+            GB_CHECK(launch<LFG_LD>(h, a, k, st, &G));
     }
     GB_CHECK(read_status(h, st));
     h->pos += a.n_pos;
@@ -793,45 +903,67 @@ int lfg_ld_stepwise(const ld_system* s, int64_t n_steps, ld_stats* out, cudaStre
         if (out) *out = ld_stats{0, 0, 0, 0, n_steps};
         return GBRNG_OK;
     }
-    const int64_t D = (int64_t)h->ll - h->sl, R = (int64_t)h->ring_mask + 1;
+    const int k = pick_order(h, kOrderStep);
+    const int64_t D = (int64_t)h->ll - h->sl;
     const int64_t four_n = 4 * s->n;
-    if (four_n > std::min(2 * D, R - 2 * (int64_t)h->ll) || (h->pos < h->ll && four_n > D))
+    if (four_n > round_width(h, k, 0))
         return fail(GBRNG_ELAGS,
-                    "one launch per step needs 4N = %lld within the lag distance (ll - sl = %lld, "
-                    "twice that from position ll on)",
-                    (long long)four_n, (long long)D);
+                    "one launch per step needs 4N = %lld within %d times the lag distance "
+                    "(ll - sl = %lld)",
+                    (long long)four_n, k, (long long)D);
     GB_CHECK(ensure_eacc(h, s->n));
     GB_CUDA(cudaMemsetAsync(h->eacc, 0, sizeof(float2) * s->n, st));
     LfgArgs a{};
-    set_ring(h, a);
+    set_ring(h, a, k);
     a.N = s->n;
     a.x = s->x;
     a.v = s->v;
     a.Kper = s->K_per;
     a.c = make_coef(s);
     const unsigned blocks = (unsigned)((s->n + 255) / 256);
-    for (int64_t t = 0; t < n_steps; ++t)
-        lfg_step_kernel<<<blocks, 256, 0, st>>>(a, h->pos + four_n * t, h->eacc);
+    uint32_t sP = a.base_slot;
+    for (int64_t t = 0; t < n_steps; ++t) {
+        if (k == 1)
+            lfg_step_kernel<1><<<blocks, 256, 0, st>>>(a, sP, h->eacc);
+        else if (k == 2)
+            lfg_step_kernel<2><<<blocks, 256, 0, st>>>(a, sP, h->eacc);
+        else
+            lfg_step_kernel<4><<<blocks, 256, 0, st>>>(a, sP, h->eacc);
+        sP = slot_add(sP, (uint32_t)four_n, a.R);
+    }
     GB_CUDA(cudaGetLastError());
     h->pos += four_n * n_steps;
     return stepwise_stats(h, s, n_steps, out, st);
+}
+
+template <int K>
+static int launch_ou(Handle* h, LfgArgs& a, OuCoef c, float* Rp, float* R0, int64_t ev,
+                     double* parts, int64_t G, cudaStream_t st)
+{
+    void* args[] = {&a, &c, &Rp, &R0, &ev, &parts};
+    GB_CUDA(cudaLaunchCooperativeKernel((const void*)lfg_ou_kernel<K>, dim3((unsigned)G), dim3(256),
+                                        args, 0, st));
+    return GBRNG_OK;
 }
 
 int lfg_ou(const ou_system* s, int64_t n_steps, int64_t every, double* mean, double* corr,
            cudaStream_t st)
 {
     Handle* h = s->rng;
-    const int64_t D = (int64_t)h->ll - h->sl, Rsz = (int64_t)h->ring_mask + 1;
+    const int k = pick_order(h, kOrderOu);
+    const int64_t D = (int64_t)h->ll - h->sl;
     const int64_t two_n = 2 * s->n;
-    if (two_n > std::min(2 * D, Rsz - 2 * (int64_t)h->ll) || (h->pos < h->ll && two_n > D))
+    if (two_n > round_width(h, k, 0))
         return fail(GBRNG_ELAGS,
-                    "one round per step needs 2N = %lld within the lag distance (ll - sl = %lld, "
-                    "twice that from position ll on)",
-                    (long long)two_n, (long long)D);
+                    "one round per step needs 2N = %lld within %d times the lag distance "
+                    "(ll - sl = %lld)",
+                    (long long)two_n, k, (long long)D);
     DevInfo di;
     GB_CHECK(dev_info(h->device, &di));
     int occ = 0;
-    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lfg_ou_kernel, 256, 0));
+    const void* fn = k == 1 ? (const void*)lfg_ou_kernel<1>
+                            : k == 2 ? (const void*)lfg_ou_kernel<2> : (const void*)lfg_ou_kernel<4>;
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, 256, 0));
     if (occ < 1) return fail(GBRNG_EINVAL, "overdamped kernel does not fit on an SM");
     const int64_t G = std::min<int64_t>((int64_t)di.sms * occ, (s->n + 255) / 256);
     const bool rec = mean != nullptr;
@@ -846,17 +978,18 @@ int lfg_ou(const ou_system* s, int64_t n_steps, int64_t every, double* mean, dou
     float* R0 = reinterpret_cast<float*>(h->eacc);
     GB_CUDA(cudaMemcpyAsync(R0, s->R, sizeof(float) * s->n, cudaMemcpyDeviceToDevice, st));
     LfgArgs a{};
-    set_ring(h, a);
+    set_ring(h, a, k);
     a.N = s->n;
     a.n_steps = n_steps;
     GB_CHECK(launch_common(h, a, G, st));
-    OuCoef c = make_ou_coef(s);
-    float* Rp = s->R;
-    int64_t ev = every;
+    const OuCoef c = make_ou_coef(s);
     double* parts = rec ? h->partials : nullptr;
-    void* args[] = {&a, &c, &Rp, &R0, &ev, &parts};
-    GB_CUDA(cudaLaunchCooperativeKernel((const void*)lfg_ou_kernel, dim3((unsigned)G), dim3(256),
-                                        args, 0, st));
+    if (k == 1)
+        GB_CHECK(launch_ou<1>(h, a, c, s->R, R0, every, parts, G, st));
+    else if (k == 2)
+        GB_CHECK(launch_ou<2>(h, a, c, s->R, R0, every, parts, G, st));
+    else
+        GB_CHECK(launch_ou<4>(h, a, c, s->R, R0, every, parts, G, st));
     GB_CHECK(read_status(h, st));
     h->pos += two_n * n_steps;
     if (rec) return ou_finish(h, s->n, n_rec, G, mean, corr, st);
@@ -864,3 +997,13 @@ int lfg_ou(const ou_system* s, int64_t n_steps, int64_t every, double* mean, dou
 }
 
 }  // namespace gb
+
+using namespace gb;
+
+extern "C" int gbrng_set_lfg_order(int k)
+{
+    if (k != 0 && k != 1 && k != 2 && k != 4)
+        return fail(GBRNG_EINVAL, "Lagged Fibonacci leap order must be 0 (automatic), 1, 2 or 4");
+    g_lfg_order.store(k);
+    return GBRNG_OK;
+}

@@ -214,15 +214,17 @@ static int alloc_state(Handle* h)
     } else if (h->kind == GBRNG_LCG) {
         e = cudaMalloc(&h->lcg, sizeof(uint32_t) * h->n);
     } else {
-        // ring size: power of two >= 2 ll + 2 D + 16384 words.  The leap reads
-        // back to p - 2 ll, and a round of W <= 2 D positions overwrites
-        // positions p - R, so R - 2 ll >= 2 D lets every round take its full
-        // width (the margin keeps overwritten values well behind readers).
+        // ring size: k (ll + D) rounded up to 32 words for the highest leap
+        // order k the ring serves (2 unless order 4 was set before creation).
+        // The order-k leap reads back to p - k ll, and a round of W <= k D
+        // positions overwrites positions p - R, so R - k ll >= k D lets every
+        // round take its full width (the seeds' backward extension fills
+        // positions -k ll .. -1).
+        h->order_max = lfg_order_for_new_handle();
         const uint64_t D = (uint64_t)(h->ll - h->sl);
-        uint64_t R = 1;
-        while (R < 2 * (uint64_t)h->ll + 2 * D + 16384u) R <<= 1;
-        h->ring_mask = (uint32_t)(R - 1);
-        e = cudaMalloc(&h->ring, sizeof(uint32_t) * R);
+        const uint64_t R = ((uint64_t)h->order_max * ((uint64_t)h->ll + D) + 31) & ~(uint64_t)31;
+        h->ring_size = (uint32_t)R;
+        e = cudaMalloc(&h->ring, sizeof(uint32_t) * (R + ring_mirror(h->ring_size)));
     }
     if (e == cudaSuccess) e = cudaMalloc(&h->dstatus, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&h->dstats, sizeof(double) * 8);
@@ -424,7 +426,8 @@ int rng_clone(gbrng_t src, gbrng_t* out, void* stream)
     else if (h->kind == GBRNG_LCG)
         e = cudaMemcpyAsync(h->lcg, src->lcg, sizeof(uint32_t) * h->n, cudaMemcpyDeviceToDevice, st);
     else
-        e = cudaMemcpyAsync(h->ring, src->ring, sizeof(uint32_t) * ((size_t)h->ring_mask + 1),
+        e = cudaMemcpyAsync(h->ring, src->ring,
+                            sizeof(uint32_t) * ((size_t)h->ring_size + ring_mirror(h->ring_size)),
                             cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) {
         free_handle(h);
@@ -489,12 +492,14 @@ int rng_get_state(gbrng_t rng, void* host, size_t bytes)
         for (int64_t s = 0; s < rng->n; ++s)
             for (int k = 0; k < 35; ++k) o[35 * s + k] = tmp[(size_t)k * rng->n + s];
     } else {
-        const uint64_t R = (uint64_t)rng->ring_mask + 1;
+        const int64_t R = rng->ring_size;
         std::vector<uint32_t> ring(R);
         GB_CUDA(cudaMemcpy(ring.data(), rng->ring, sizeof(uint32_t) * R, cudaMemcpyDeviceToHost));
         uint32_t* o = (uint32_t*)dst;
-        for (int64_t k = 0; k < rng->ll; ++k)
-            o[k] = ring[(uint64_t)(rng->pos - rng->ll + k) & rng->ring_mask];
+        for (int64_t k = 0; k < rng->ll; ++k) {
+            const int64_t r = (rng->pos - rng->ll + k) % R;
+            o[k] = ring[r < 0 ? r + R : r];
+        }
     }
     return GBRNG_OK;
 }
@@ -525,21 +530,26 @@ int rng_set_state(gbrng_t rng, const void* host, size_t bytes)
             for (int k = 0; k < 35; ++k) tmp[(size_t)k * rng->n + s] = in[35 * s + k];
         GB_CUDA(cudaMemcpy(rng->r2, tmp.data(), pb, cudaMemcpyHostToDevice));
     } else {
-        // The blob holds x_{p-ll} .. x_{p-1}.  The leap form of the recurrence
-        // also reads x_{p-2ll} .. x_{p-ll-1}; they follow from the recurrence
-        // run backwards, x_q = x_{q+ll} - x_{q+sl}, exact for every q >= -ll.
-        const uint64_t R = (uint64_t)rng->ring_mask + 1;
-        const int64_t ll = rng->ll, sl = rng->sl, p = hd.position;
-        std::vector<uint32_t> hist(2 * (size_t)ll);          // hist[j] = x_{p-2ll+j}
+        // The blob holds x_{p-ll} .. x_{p-1}.  The leap forms of the recurrence
+        // also read x_{p-k ll} .. x_{p-ll-1} (k = the ring's highest order);
+        // they follow from the recurrence run backwards, x_q = x_{q+ll} -
+        // x_{q+sl}, which keeps the recurrence true at every index the leaps use.
+        const int64_t R = rng->ring_size;
+        const int64_t ll = rng->ll, sl = rng->sl, p = hd.position, k = rng->order_max;
+        std::vector<uint32_t> hist((size_t)k * ll);          // hist[j] = x_{p-k ll+j}
         const uint32_t* in = (const uint32_t*)src;
-        for (int64_t k = 0; k < ll; ++k) hist[ll + k] = in[k];
-        for (int64_t j = ll - 1; j >= 0; --j) hist[j] = hist[j + ll] - hist[j + sl];
-        std::vector<uint32_t> ring(R, 0u);
-        for (int64_t j = 0; j < 2 * ll; ++j) {
-            const int64_t q = p - 2 * ll + j;
-            if (q >= -ll) ring[(uint64_t)q & rng->ring_mask] = hist[j];
+        for (int64_t i = 0; i < ll; ++i) hist[(k - 1) * ll + i] = in[i];
+        for (int64_t j = (k - 1) * ll - 1; j >= 0; --j) hist[j] = hist[j + ll] - hist[j + sl];
+        const int64_t M = ring_mirror(rng->ring_size);
+        std::vector<uint32_t> ring(R + M, 0u);
+        for (int64_t j = 0; j < k * ll; ++j) {
+            int64_t r = (p - k * ll + j) % R;
+            if (r < 0) r += R;
+            ring[r] = hist[j];
+            if (r < M) ring[r + R] = hist[j];
         }
-        GB_CUDA(cudaMemcpy(rng->ring, ring.data(), sizeof(uint32_t) * R, cudaMemcpyHostToDevice));
+        GB_CUDA(cudaMemcpy(rng->ring, ring.data(), sizeof(uint32_t) * (R + M),
+                           cudaMemcpyHostToDevice));
         rng->pos = hd.position;
     }
     return GBRNG_OK;

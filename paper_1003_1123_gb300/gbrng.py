@@ -72,6 +72,7 @@ SIGNATURES = {
     "rng_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "rng_set_wait_limit_ns": (C.c_int, [C.c_uint64]),
     "gbrng_test_stall_chunk": (C.c_int, [C.c_int64]),
+    "gbrng_set_lfg_order": (C.c_int, [C.c_int]),
     "ld_init_equilibrium": (C.c_int, [C.POINTER(LdSystemC), C.c_void_p]),
     "ld_run": (C.c_int, [C.POINTER(LdSystemC), C.c_int64, C.POINTER(LdStatsC), C.c_void_p]),
     "ld_run_stepwise": (C.c_int, [C.POINTER(LdSystemC), C.c_int64, C.POINTER(LdStatsC),
@@ -245,6 +246,12 @@ def ld_set_adjoint_history_limit(nbytes: int):
     """Largest noise history ld_backward keeps (bytes; 0 always regenerates,
     -1 half the free device memory)."""
     _check(lib().ld_set_adjoint_history_limit(nbytes))
+
+
+def gbrng_set_lfg_order(k: int):
+    """Leap order of every Lagged Fibonacci launch (1, 2 or 4; 0 = each
+    launch's own choice).  Every order gives the same sequence."""
+    _check(lib().gbrng_set_lfg_order(k))
 
 
 def gbrng_test_stall_chunk(chunk: int):

@@ -67,6 +67,8 @@ def test_invalid_arguments_rejected_before_any_device_work(G):
     assert lib.rng_init_lfg(C.byref(h), 1, 10, 11, None) == -5
     assert lib.ld_run(None, 10, None, None) == -1
     assert lib.ld_run_noalloc(None, 10, None, None) == -1
+    assert lib.gbrng_set_lfg_order(3) == -1
+    assert lib.gbrng_set_lfg_order(0) == 0
     assert lib.rng_fill_u32(None, None, 10, None) == -1
     assert lib.rng_set_wait_limit_ns(0) == -1
     assert lib.rng_set_wait_limit_ns(2_000_000_000) == 0

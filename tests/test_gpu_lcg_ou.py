@@ -94,8 +94,10 @@ def test_ou_matches_oracle(G, kind):
 
 
 def test_ou_lagfib_rejects_dependent_rounds(G):
-    r = G.rng_init_lfg(4, 2000, lag_row=0)      # ll - sl = 1029 < 2N = 4000
-    s = G.OuSystem(r, torch.zeros(2000, dtype=torch.float32, device="cuda"))
+    """A step of 2N positions must fit one round: 2N <= 4 (ll - sl) = 4116 on
+    row 0 (the order-4 leap), so N = 2100 is refused."""
+    r = G.rng_init_lfg(4, 2100, lag_row=0)
+    s = G.OuSystem(r, torch.zeros(2100, dtype=torch.float32, device="cuda"))
     with pytest.raises(G.GbrngError) as e:
         G.ou_run(s, 10, 5)
     assert e.value.code == -5

@@ -297,13 +297,14 @@ def test_lagfib_timeouts_on_every_cooperative_kernel(G, path):
     x = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
     s = G.LdSystem(r, x, torch.zeros_like(x))
     G.ld_init_equilibrium(s)
-    G.rng_fill_u32(r, 4 * 10**6)           # past ll: the fused run takes the resident kernel
+    G.rng_fill_u32(r, 4 * 10**6)
     G.rng_set_wait_limit_ns(200_000_000)
     G.gbrng_test_stall_chunk(5)
     try:
         with pytest.raises(G.GbrngError) as e:
             if path == "resident":
-                G.ld_run(s, 20, stats=False)
+                # a round holds up to 4 (ll - sl) / 4N = 20 steps of 1e5 oscillators
+                G.ld_run(s, 100, stats=False)
             elif path == "fill":
                 G.rng_fill_uniform(r, 32 * 10**6)
             else:

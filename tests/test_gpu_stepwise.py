@@ -69,7 +69,7 @@ def test_stepwise_matches_oracle(G):
 
 
 def test_stepwise_lagfib_rejects_dependent_steps(G):
-    """Row 0 has ll - sl = 1029: 4N = 4800 > 2(ll - sl) cannot run one step per launch."""
+    """Row 0 has ll - sl = 1029: 4N = 4800 > 4(ll - sl) cannot run one step per launch."""
     r = G.rng_init_lfg(5, 1200, lag_row=0)
     x = torch.zeros((1200, 3), dtype=torch.float32, device="cuda")
     s = G.LdSystem(r, x, torch.zeros_like(x))
