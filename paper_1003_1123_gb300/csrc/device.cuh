@@ -74,17 +74,19 @@ __host__ __device__ __forceinline__ int32_t schrage(int32_t x)
 }
 
 // The same a*x mod m from the 64-bit product, for m = 2^31 - d: 2^31 = d
-// (mod m), so p = hi 2^31 + lo = hi d + lo (mod m), and hi d + lo < 2^31 + 2^24
-// < 2m needs one conditional subtraction.  Equal to schrage() for every
-// 0 < x < m (checked exhaustively for both moduli); one wide multiply instead
-// of Schrage's quotient and three multiplies.
+// (mod m), so p = hi 2^31 + lo = hi d + lo (mod m), and r = hi d + lo <
+// 2^31 + 2^24 < 2m needs one conditional subtraction, taken as the unsigned
+// minimum of r and r - m (for r < m the difference wraps above r).  Equal to
+// schrage() for every 0 < x < m (checked exhaustively for both moduli); one
+// wide multiply instead of Schrage's quotient and three multiplies.
 template <int32_t A, int32_t M>
 __host__ __device__ __forceinline__ int32_t mulmod_m31(int32_t x)
 {
     constexpr uint32_t d = 2147483648u - (uint32_t)M;
     const uint64_t p = (uint64_t)(uint32_t)A * (uint32_t)x;
     const uint32_t r = (uint32_t)(p >> 31) * d + ((uint32_t)p & 0x7fffffffu);
-    return (int32_t)(r >= (uint32_t)M ? r - (uint32_t)M : r);
+    const uint32_t rm = r - (uint32_t)M;
+    return (int32_t)(rm < r ? rm : r);
 }
 
 // One Ran2 draw; the shuffle table is addressed through `iv(j)` so that it can

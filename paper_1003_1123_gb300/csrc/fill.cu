@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(128) ran2_fill_kernel(int32_t* __restrict__ st
         Ran2Regs r{st[s], st[S + s], st[2 * S + s]};
 #pragma unroll 4
         for (int j = 0; j < 32; ++j) iv(j) = st[(3 + j) * S + s];
-        for (int64_t idx = s; idx < n_items; idx += S) {
+        auto emit = [&](int64_t idx) {
             if (MODE == FILL_U32) {
                 ((uint32_t*)out)[idx] = (uint32_t)ran2_next(r, iv);
             } else if (MODE == FILL_UNIFORM) {
@@ -74,7 +74,16 @@ __global__ void __launch_bounds__(128) ran2_fill_kernel(int32_t* __restrict__ st
                 box_muller(u1, u2, g.x, g.y);
                 ((float2*)out)[idx] = g;
             }
+        };
+        int64_t idx = s;
+        // four draws a loop iteration: one bound check for four stores
+        for (; idx + 3 * S < n_items; idx += 4 * S) {
+            emit(idx);
+            emit(idx + S);
+            emit(idx + 2 * S);
+            emit(idx + 3 * S);
         }
+        for (; idx < n_items; idx += S) emit(idx);
         st[s] = r.idum;
         st[S + s] = r.idum2;
         st[2 * S + s] = r.iy;
