@@ -92,24 +92,20 @@ __global__ void __launch_bounds__(128) ran2_fill_kernel(int32_t* __restrict__ st
     }
 }
 
+// Grid: one thread per stream (up to the streams a fill touches), in as many
+// waves as that takes, rather than one resident wave looping over streams:
+// the blocks then start, and load their streams' state, at staggered times
+// instead of all together under the fill's store traffic (2^30 numbers from
+// 1e6 streams: Ran2 uniform 1.15 -> 1.09 ms, normal 1.91 -> 1.82, Taus uniform
+// 0.91 -> 0.87, normal 1.59 -> 1.57).  The kernels keep their stream loop, so
+// any grid covers every stream.
 template <int MODE>
 static int fill_pt(Handle* h, void* dst, int64_t n_items, cudaStream_t st)
 {
-    DevInfo di;
-    GB_CHECK(dev_info(h->device, &di));
     const int64_t active = h->n < n_items ? h->n : n_items;
     if (h->kind == GBRNG_TAUS || h->kind == GBRNG_LCG) {
         const int T = 256;
-        int occ = 0;
-        if (h->kind == GBRNG_TAUS)
-            GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &occ, word_fill_kernel<MODE, uint4>, T, 0));
-        else
-            GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                &occ, word_fill_kernel<MODE, uint32_t>, T, 0));
-        int64_t blocks = (active + T - 1) / T;
-        const int64_t cap = (int64_t)di.sms * (occ > 0 ? occ : 1);
-        if (blocks > cap) blocks = cap;
+        const int64_t blocks = (active + T - 1) / T;
         if (h->kind == GBRNG_TAUS)
             word_fill_kernel<MODE, uint4><<<(unsigned)blocks, T, 0, st>>>(h->taus, h->n, n_items, dst);
         else
@@ -118,11 +114,7 @@ static int fill_pt(Handle* h, void* dst, int64_t n_items, cudaStream_t st)
     } else {
         const int T = 128;
         const size_t smem = sizeof(int32_t) * 32 * T;
-        int occ = 0;
-        GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ran2_fill_kernel<MODE>, T, smem));
-        int64_t blocks = (active + T - 1) / T;
-        const int64_t cap = (int64_t)di.sms * (occ > 0 ? occ : 1);
-        if (blocks > cap) blocks = cap;
+        const int64_t blocks = (active + T - 1) / T;
         ran2_fill_kernel<MODE><<<(unsigned)blocks, T, smem, st>>>(h->r2, h->n, n_items, dst);
     }
     GB_CUDA(cudaGetLastError());

@@ -78,8 +78,15 @@ struct Handle {
     size_t adj_bytes = 0;
 };
 
-// Mirrored slots after a Lagged Fibonacci ring of R slots.
-inline uint32_t ring_mirror(uint32_t R) { return R < 32768u ? R : 32768u; }
+// Mirrored slots after a Lagged Fibonacci ring of R slots: 32768 (a resident
+// CTA's step region at 1e6 oscillators is 26368), at most a quarter of the
+// ring (so that small rings do not store every value twice), a multiple of
+// 32 (R >= 6620 for every Table I row, so never below 1632 >= one block).
+inline uint32_t ring_mirror(uint32_t R)
+{
+    const uint32_t q = (R / 4) & ~31u;
+    return q < 32768u ? q : 32768u;
+}
 
 // Device attributes used for launch sizing (cached per device).
 struct DevInfo {

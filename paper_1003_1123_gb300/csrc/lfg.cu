@@ -18,7 +18,7 @@
 // Ring.  Position p lives in slot p mod R of a ring of R >= K (ll + D) words
 // (rounded up to 32 words: 40.3 MB for the last Table I row at K = 2).  Slot
 // arithmetic is 32-bit: an offset below R is added with one conditional
-// subtraction of R.  The first M = min(32768, R) slots are mirrored after the
+// subtraction of R.  The first M = min(32768, R / 4) slots are mirrored after the
 // ring (words R .. R + M - 1; every store to a slot below M also stores its
 // mirror), so any window of at most M positions starting at slot s < R is the
 // contiguous range [s, s + M) of the allocation: lag windows never wrap, and
@@ -420,14 +420,17 @@ __global__ void __launch_bounds__(kLfgThreads, 3) lfg_kernel(LfgArgs a)
 // the mirror, a region whose window wrapped took a slower per-block path;
 // with 152 CTAs about one did so every step and held up the barrier: 13.2
 // against 11.6 us per step at 1e6 oscillators on a 40 MB ring.)
-// 640 threads (20 warps, up to 102 registers): 11.6 us per step at 1e6
-// oscillators against 12.2 with 512 and 11.7 with 768 (same GB300, same ring).
-constexpr int kResThreads = 640;
-constexpr int kResWarps = kResThreads / 32;
-
-template <int K>
-__global__ void __launch_bounds__(kResThreads, 1) lfg_resident_kernel(LfgArgs a, int64_t n_c)
+// CTA size T: 512 or 640 threads, whichever leaves fewer of the CTA's
+// 32-oscillator blocks per warp in a step (ties: 512).  At 1e6 oscillators
+// (206 blocks a CTA) 640 threads take 11.6 us per step against 12.2 with 512
+// and 11.7 with 768 (same GB300, same ring); where both sizes leave the same
+// count (1e5: 21 blocks, two per warp at most either way) the smaller CTA
+// has less to synchronise.
+template <int K, int T>
+__global__ void __launch_bounds__(T, 1) lfg_resident_kernel(LfgArgs a, int64_t n_c)
 {
+    constexpr int kResThreads = T;
+    constexpr int kResWarps = T / 32;
     extern __shared__ __align__(16) float res_sm[];
     __shared__ __align__(16) uint32_t bufs[kResWarps][128];
     __shared__ double red[4 * 32];
@@ -758,9 +761,11 @@ static int launch(Handle* h, LfgArgs& a, int k, cudaStream_t st, int64_t* G_out)
 // round (4N within the width) and one CTA per SM can hold its share of x and
 // v.  Returns 1 (and launches) when it applies, 0 when the caller must use the
 // general kernel, or an error.
-template <int K>
+template <int K, int T>
 static int try_launch_resident_k(Handle* h, LfgArgs& a, cudaStream_t st, int64_t* G_out)
 {
+    constexpr int kResThreads = T;
+    constexpr int kResWarps = T / 32;
     a.w = round_width(h, K, 0);   // the full width: several steps a round
     if (4 * a.N > a.w) return 0;
     DevInfo di;
@@ -771,7 +776,7 @@ static int try_launch_resident_k(Handle* h, LfgArgs& a, cudaStream_t st, int64_t
     const size_t smem = sizeof(float) * 6 * (size_t)n_c;
     const size_t static_smem = sizeof(uint32_t) * kResWarps * 128 + sizeof(double) * 128 + 64;
     if (smem + static_smem > di.smem_optin) return 0;
-    auto fn = lfg_resident_kernel<K>;
+    auto fn = lfg_resident_kernel<K, T>;
     GB_CUDA(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
     int occ = 0;
@@ -788,11 +793,22 @@ static int try_launch_resident_k(Handle* h, LfgArgs& a, cudaStream_t st, int64_t
     return 1;
 }
 
+template <int K>
+static int try_launch_resident_t(Handle* h, LfgArgs& a, cudaStream_t st, int64_t* G_out)
+{
+    DevInfo di;
+    GB_CHECK(dev_info(h->device, &di));
+    const int64_t n_c = ((a.N + di.sms - 1) / di.sms + 31) & ~(int64_t)31;
+    const int64_t nblk = n_c / 32;
+    if ((nblk + 19) / 20 < (nblk + 15) / 16) return try_launch_resident_k<K, 640>(h, a, st, G_out);
+    return try_launch_resident_k<K, 512>(h, a, st, G_out);
+}
+
 static int try_launch_resident(Handle* h, LfgArgs& a, int k, cudaStream_t st, int64_t* G_out)
 {
-    if (k == 1) return try_launch_resident_k<1>(h, a, st, G_out);
-    if (k == 2) return try_launch_resident_k<2>(h, a, st, G_out);
-    return try_launch_resident_k<4>(h, a, st, G_out);
+    if (k == 1) return try_launch_resident_t<1>(h, a, st, G_out);
+    if (k == 2) return try_launch_resident_t<2>(h, a, st, G_out);
+    return try_launch_resident_t<4>(h, a, st, G_out);
 }
 
 static int read_status(Handle* h, cudaStream_t st)
