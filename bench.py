@@ -76,7 +76,7 @@ INT_OPS_PER_DRAW = {"taus": 11, "ran2": 8}
 INT_OPS_PER_OSC_STEP = {k: 4 * v for k, v in INT_OPS_PER_DRAW.items()}
 # Algorithmic bytes per oscillator-step of the Lagged Fibonacci fused step at
 # 1e6 oscillators: four ring values, each 2 lag reads + 1 write of 4 B = 48 B
-# (x and v stay in shared memory for the whole launch).  The ring (64 MiB for
+# (x and v stay in shared memory for the whole launch).  The ring (40 MB for
 # the last Table I row) stays in L2, so the bound is L2 bandwidth, measured
 # below as a device-to-device copy of 2 x 32 MiB that stays L2-resident.
 LFG_BYTES_PER_OSC_STEP = 48

@@ -4,7 +4,8 @@ how many lag reads a value costs and how many positions a barrier round
 holds: orders 1, 2 and 4 give the oracle's serial sequence bit for bit in the
 fills, the fused step (general and resident-state kernels), the paper form
 and the overdamped run, from a fresh seed and from a restored state (whose
-backward extension to x_{p-4ll} is rebuilt on the host)."""
+backward extension to x_{p-K ll}, K the ring's highest order, is rebuilt on
+the host)."""
 import numpy as np
 import pytest
 import torch
@@ -118,3 +119,27 @@ def test_order_setting_rejects_other_values(G):
             G.gbrng_set_lfg_order(bad)
         assert e.value.code == -1
     G.gbrng_set_lfg_order(0)
+
+
+def test_state_blob_moves_between_ring_orders(G):
+    """A state blob holds the last ll values only, so it moves between a
+    handle whose ring serves order 4 and one that serves order 2 (each rebuilds
+    its own backward extension); both continue the oracle's sequence."""
+    row, n = 5, 300
+    sl, ll = oracle.lfg_table(row)
+    g = oracle.Gen("lagfib", 61, n, lag_row=row)
+    try:
+        G.gbrng_set_lfg_order(4)
+        r4 = G.rng_init_lfg(61, n, row)
+        a = 3 * ll + 11
+        assert np.array_equal(u32(G.rng_fill_u32(r4, a)), g.fill_u32(a))   # order 4
+        G.gbrng_set_lfg_order(0)
+        r2 = G.rng_init_lfg(62, n, row)
+        G.rng_set_state(r2, G.rng_get_state(r4))
+        b = 4 * ll + 5
+        assert np.array_equal(u32(G.rng_fill_u32(r2, b)), g.fill_u32(b))
+        G.gbrng_set_lfg_order(4)
+        G.rng_set_state(r4, G.rng_get_state(r2))
+        assert np.array_equal(u32(G.rng_fill_u32(r4, b)), g.fill_u32(b))
+    finally:
+        G.gbrng_set_lfg_order(0)
