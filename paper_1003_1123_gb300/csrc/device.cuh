@@ -424,6 +424,11 @@ __device__ __forceinline__ void red_release_add_u64(uint64_t* p, uint64_t v)
     asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+__device__ __forceinline__ void st_release_u64(uint64_t* p, uint64_t v)
+{
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 __device__ __forceinline__ uint64_t ld_relaxed_u64(const uint64_t* p)
 {
     uint64_t v;

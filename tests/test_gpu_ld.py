@@ -287,12 +287,15 @@ def test_lagfib_timeout_reported_without_fault(G):
     assert G.rng_fill_u32(r2, 10**6).numel() == 10**6
 
 
-@pytest.mark.parametrize("path", ["resident", "fill", "ou"])
+@pytest.mark.parametrize("path", ["resident", "resident_dataflow", "fill", "ou"])
 def test_lagfib_timeouts_on_every_cooperative_kernel(G, path):
-    """The stall hook (one CTA never arrives at the grid barrier) ends the
-    resident-state fused kernel, the fill rounds and the overdamped run with
-    GBRNG_ETIMEOUT after the wait limit; the context stays usable."""
-    n = 10**5
+    """The stall hook (one CTA never arrives at the grid barrier, or never
+    publishes its steps to the CTAs that wait on it) ends the resident-state
+    fused kernel in both of its synchronisation modes, the fill rounds and the
+    overdamped run with GBRNG_ETIMEOUT after the wait limit; the context stays
+    usable."""
+    # 1e6 oscillators: one step a round, so the resident kernel waits per CTA
+    n = 10**6 if path == "resident_dataflow" else 10**5
     r = G.rng_init("lagfib", 9, n)
     x = torch.zeros((n, 3), dtype=torch.float32, device="cuda")
     s = G.LdSystem(r, x, torch.zeros_like(x))
@@ -302,7 +305,7 @@ def test_lagfib_timeouts_on_every_cooperative_kernel(G, path):
     G.gbrng_test_stall_chunk(5)
     try:
         with pytest.raises(G.GbrngError) as e:
-            if path == "resident":
+            if path.startswith("resident"):
                 # a round holds up to 4 (ll - sl) / 4N = 20 steps of 1e5 oscillators
                 G.ld_run(s, 100, stats=False)
             elif path == "fill":
