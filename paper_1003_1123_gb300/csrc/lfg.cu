@@ -224,7 +224,7 @@ __device__ __forceinline__ uint4 block_transpose(const uint32_t* buf)
     return w;
 }
 
-// Walk this warp's blocks b = first, first + step, ... < nblk of a region of
+// Walk this warp's blocks b = first, first + step, ... < min(nblk, end) of a region of
 // n_region positions whose first position lives in slot s_first (block b
 // starts 128 b later, 128 b < n_region <= R), with the lag loads of the next
 // kLfgDepth - 1 blocks in flight while one is consumed.  Positions of one
@@ -232,9 +232,10 @@ __device__ __forceinline__ uint4 block_transpose(const uint32_t* buf)
 // consume(b, nval, w) receives lane's four values after they are stored.
 template <int K, class F>
 __device__ __forceinline__ void walk_blocks(const LfgArgs& a, uint32_t s_first, int64_t n_region,
-                                            int64_t first, int64_t step, uint32_t* buf, F&& consume)
+                                            int64_t first, int64_t step, int64_t end, uint32_t* buf,
+                                            F&& consume)
 {
-    const int64_t nblk = (n_region + 127) >> 7;
+    const int64_t nblk = min((n_region + 127) >> 7, end);   // blocks first, first + step, ... < end
     Lags<K> pipe[kLfgDepth][4];
     int nv[kLfgDepth];
     uint32_t sl[kLfgDepth];
@@ -294,6 +295,55 @@ __device__ __forceinline__ void em_update(const LdCoef& c, float Ki, float g0, f
     }
 }
 
+// Dataflow wait of the round kernel (order 2 on the exact ring, a.prog set).
+// In this mode CTA c owns the contiguous blocks [c B / G, (c + 1) B / G) of each
+// round of B blocks, and publishes prog[c] = rounds it has completed.  Its
+// share [q_lo, q_hi) (launch offsets) of round r reads the lag windows
+// [q - back_j] (back_j = (2-j) ll + j D), all in earlier rounds (W <= 2D); with
+// the exact ring the reads of the values its stores overwrite are the
+// positions q - back_j - r (r < 32); and in the fused step its oscillators'
+// x, v were last written one step (4N >= W) earlier.  So the CTA waits until
+// the owners of [q_lo - back_j - 32, q_hi - back_j) for the three windows, and
+// of [q_lo - 4N, q_hi - 4N) in the fused step, have completed those rounds:
+// threads 4j .. 4j + 3 each take every fourth owner of window j.  Bounded by
+// the launch's wait limit; returns false on failure (GBRNG_ETIMEOUT recorded).
+__device__ bool round_dataflow_wait(const LfgArgs& a, int64_t q_lo, int64_t q_hi, bool ld)
+{
+    const int nwin = ld ? 4 : 3;
+    if (threadIdx.x >= 4 * nwin) return true;
+    const int jw = threadIdx.x >> 2, m = threadIdx.x & 3;
+    const int64_t D = (int64_t)a.ll - a.sl;
+    const int64_t back = jw < 3 ? (int64_t)(2 - jw) * a.ll + (int64_t)jw * D : 4 * a.N;
+    int64_t lo = q_lo - back - 32;
+    const int64_t hi = q_hi - back;
+    if (lo < 0) lo = 0;   // positions before the launch are complete
+    if (hi <= lo) return true;
+    const int64_t G = gridDim.x;
+    // (round, owner CTA) of launch offset q as one increasing index
+    auto owner = [&](int64_t q) {
+        const int64_t r = q / a.w, blk = (q - r * a.w) >> 7;
+        const int64_t nb = (min(a.w, a.n_pos - r * a.w) + 127) >> 7;
+        return r * G + ((blk + 1) * G - 1) / nb;
+    };
+    const int64_t L0 = owner(lo), L1 = owner(hi - 1);
+    const uint64_t deadline = global_ns() + a.wait_ns;
+    for (int64_t L = L0 + m; L <= L1; L += 4) {
+        const uint64_t* f = a.prog + (L % G);
+        const uint64_t need = (uint64_t)(L / G) + 1;
+        for (uint32_t n = 1; ld_relaxed_u64(f) < need; ++n) {
+            if ((n & 15u) == 0) {
+                if (ld_volatile_i32(a.status) != DEV_OK) return false;
+                if (global_ns() > deadline) {
+                    atomicCAS(a.status, DEV_OK, DEV_TIMEOUT);
+                    return false;
+                }
+            }
+        }
+        (void)ld_acquire_u64(f);
+    }
+    return true;
+}
+
 template <int MODE, int K>
 __global__ void __launch_bounds__(kLfgThreads, 3) lfg_kernel(LfgArgs a)
 {
@@ -304,6 +354,8 @@ __global__ void __launch_bounds__(kLfgThreads, 3) lfg_kernel(LfgArgs a)
     const int64_t gwarp = blockIdx.x * (int64_t)kLfgWarps + warp;
     const int64_t nwarps = (int64_t)gridDim.x * kLfgWarps;
     const bool arrive_here = (int)blockIdx.x != a.stall_cta;
+    __shared__ int s_df_fail;
+    if (threadIdx.x == 0) s_df_fail = 0;
     Kahan e;
     double acc[3] = {0, 0, 0};
     uint64_t round = 0;
@@ -311,8 +363,23 @@ __global__ void __launch_bounds__(kLfgThreads, 3) lfg_kernel(LfgArgs a)
     for (int64_t U = 0; U < a.n_pos; ++round) {
         // rounds: whole oscillator-steps for the fused step (U, widths are multiples of 4)
         const int64_t U1 = min(a.n_pos, U + a.w);
+        // this warp's blocks of the round: with dataflow waits the CTA's
+        // contiguous share, walked by its warps; else every warp of the grid
+        // strided over the whole round
+        const int64_t nblk_r = (U1 - U + 127) >> 7;
+        int64_t first = gwarp, step = nwarps, end = nblk_r;
+        if (a.prog) {
+            const int64_t b0 = blockIdx.x * nblk_r / gridDim.x;
+            end = (blockIdx.x + 1) * nblk_r / gridDim.x;
+            first = b0 + warp;
+            step = kLfgWarps;
+            __syncthreads();   // s_df_fail written before any thread reads it below
+            if (!round_dataflow_wait(a, U + 128 * b0, min(U1, U + 128 * end), LD)) s_df_fail = 1;
+            __syncthreads();
+            if (s_df_fail) return;
+        }
         if (!LD) {
-            walk_blocks<K>(a, s_round, U1 - U, gwarp, nwarps, bufs[warp],
+            walk_blocks<K>(a, s_round, U1 - U, first, step, end, bufs[warp],
                            [&](int64_t b, int nval, uint4 w) {
                                const int64_t u0 = U + 128 * b;   // launch offset of the block
                                if (MODE == LFG_NORMAL) {
@@ -353,8 +420,7 @@ __global__ void __launch_bounds__(kLfgThreads, 3) lfg_kernel(LfgArgs a)
                 // no SM writes it again before the next barrier.  (6% faster at
                 // 1e8 oscillators than L2-only loads; prefetching the next
                 // round's share instead was slower.)
-                const int64_t nblk_r = (U1 - U + 127) >> 7;
-                for (int64_t bb = gwarp; bb < nblk_r; bb += nwarps) {
+                for (int64_t bb = first; bb < end; bb += step) {
                     if (4 * lane < U1 - U - 128 * bb) {
                         const int64_t u = (U >> 2) + 32 * bb + lane;
                         const int64_t j = u - (t0 + (u >= u_next ? 1 : 0)) * a.N;
@@ -363,7 +429,7 @@ __global__ void __launch_bounds__(kLfgThreads, 3) lfg_kernel(LfgArgs a)
                     }
                 }
             }
-            walk_blocks<K>(a, s_round, U1 - U, gwarp, nwarps, bufs[warp],
+            walk_blocks<K>(a, s_round, U1 - U, first, step, end, bufs[warp],
                            [&](int64_t b, int nval, uint4 w) {
                                if (4 * lane >= nval) return;
                                const int64_t u = (U >> 2) + 32 * b + lane;
@@ -397,7 +463,14 @@ __global__ void __launch_bounds__(kLfgThreads, 3) lfg_kernel(LfgArgs a)
         }
         s_round = slot_add(s_round, (uint32_t)(U1 - U), a.R);
         U = U1;
-        if (U < a.n_pos && !grid_barrier(a, (uint64_t)gridDim.x * (round + 1), arrive_here)) return;
+        if (a.prog) {
+            // publish: every ring (and x, v) store of this CTA's share is done
+            __syncthreads();
+            if (threadIdx.x == 0 && arrive_here) st_release_u64(a.prog + blockIdx.x, round + 1);
+        } else if (U < a.n_pos &&
+                   !grid_barrier(a, (uint64_t)gridDim.x * (round + 1), arrive_here)) {
+            return;
+        }
     }
     if (MODE == LFG_LD && a.partials) {
         double v[4] = {acc[0], acc[1], acc[2], e.value()};
@@ -782,6 +855,11 @@ static int launch_common(Handle* h, LfgArgs& a, int64_t G, cudaStream_t st)
     return GBRNG_OK;
 }
 
+// Round kernel synchronisation: per-CTA dataflow waits (order 2 on the exact
+// ring; each CTA a contiguous share of every round) instead of the grid
+// barrier between rounds.
+constexpr bool kRoundDataflow = true;
+
 template <int MODE, int K>
 static int launch_k(Handle* h, LfgArgs& a, cudaStream_t st, int64_t* G_out)
 {
@@ -798,7 +876,14 @@ static int launch_k(Handle* h, LfgArgs& a, cudaStream_t st, int64_t* G_out)
     if (G < 1) G = 1;
     if (MODE == LFG_LD) GB_CHECK(ensure_partials(h, G));
     a.partials = MODE == LFG_LD ? h->partials : nullptr;
+    const bool dataflow = kRoundDataflow && K == 2 && h->order_max == 2;
+    if (dataflow) GB_CHECK(ensure_progress(h, 1 + G));   // before launch_common takes [0]
     GB_CHECK(launch_common(h, a, G, st));
+    a.prog = nullptr;
+    if (dataflow) {
+        a.prog = h->progress + 1;
+        GB_CUDA(cudaMemsetAsync(a.prog, 0, sizeof(uint64_t) * G, st));
+    }
     void* args[] = {&a};
     GB_CUDA(cudaLaunchCooperativeKernel((const void*)fn, dim3((unsigned)G), dim3(kLfgThreads), args,
                                         0, st));
