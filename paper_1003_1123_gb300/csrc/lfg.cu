@@ -51,8 +51,15 @@ namespace gb {
 
 enum { LFG_U32 = 0, LFG_UNIFORM = 1, LFG_NORMAL = 2, LFG_LD = 3, LFG_LD_INIT = 4 };
 
-constexpr int kLfgThreads = 256;   // three CTAs per SM: 24 warps to hide HBM latency;
-                                   // two or four CTAs per SM: fills 5-6% slower
+// Round kernel CTAs: 128 threads, eight a SM for the fused step and seven for
+// the fills (up to 64 and 73 registers; a few bytes spill).  With per-CTA
+// dataflow waits more, smaller CTAs overlap one CTA's wait with the others'
+// work: against 256 x 3 on one GB300, 1e8 oscillators 1955 -> 1865 us per
+// step, 1e7 175 -> 170, 2^30 fills 2.28 -> 2.22 ms (uniform) and 2.92 -> 2.83
+// (normal); 64 x 16 and 512 x 2 were slower.
+constexpr int kLfgThreads = 128;
+template <int MODE>
+constexpr int lfg_min_blocks() { return MODE >= LFG_LD ? 8 : 7; }
 constexpr int kLfgWarps = kLfgThreads / 32;
 constexpr int kLfgDepth = 2;     // blocks per warp with lag loads in flight
 constexpr int kMaxOrder = 4;
@@ -345,7 +352,7 @@ __device__ bool round_dataflow_wait(const LfgArgs& a, int64_t q_lo, int64_t q_hi
 }
 
 template <int MODE, int K>
-__global__ void __launch_bounds__(kLfgThreads, 3) lfg_kernel(LfgArgs a)
+__global__ void __launch_bounds__(kLfgThreads, lfg_min_blocks<MODE>()) lfg_kernel(LfgArgs a)
 {
     __shared__ __align__(16) uint32_t bufs[kLfgWarps][128];
     __shared__ double red[4 * 32];
