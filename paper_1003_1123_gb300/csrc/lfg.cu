@@ -496,39 +496,47 @@ __global__ void __launch_bounds__(kLfgThreads, lfg_min_blocks<MODE>()) lfg_kerne
 // only readers are the positions q - R + back_j = q - back_j - r: so once the
 // CTAs that computed the positions [q_lo - back_j - 32, q_hi - back_j) have
 // published, both the values this step reads (read after write) and the reads
-// of the values it overwrites (write after read) are complete.  Threads 4j .. 4j
-// + 3 each wait for every fourth of window j's producer CTAs (step s of CTA c:
-// prog[c] >= s + 1), bounded by the launch's wait limit.  Returns false on
-// failure (GBRNG_ETIMEOUT recorded).
+// of the values it overwrites (write after read) are complete.  The wait comes
+// once a round, for all kr steps of the round at once (their windows lie in
+// earlier rounds, 4N kr <= 2D), and each CTA publishes prog[c] = steps done at
+// the round's end; a producer's step s is complete once prog[c] >= s + 1.  The
+// (step, window, producer) triples are spread over the CTA's threads; every
+// poll is bounded by the launch's wait limit.  Returns false on failure
+// (GBRNG_ETIMEOUT recorded).
 template <int K>
-__device__ bool dataflow_wait(const LfgArgs& a, int64_t t, int64_t j0, int nc, int64_t n_c)
+__device__ bool dataflow_wait(const LfgArgs& a, int64_t t, int64_t kr, int64_t j0, int nc,
+                              int64_t n_c)
 {
-    if (threadIdx.x >= 4 * (K + 1)) return true;
-    const int jw = threadIdx.x >> 2, m = threadIdx.x & 3;
-    const int64_t back = (int64_t)(K - jw) * a.ll + (int64_t)jw * (a.ll - a.sl);
-    const int64_t q0 = a.base + 4 * (t * a.N + j0);
-    int64_t lo = q0 - back - 32;
-    const int64_t hi = q0 + 4 * (int64_t)nc - back;
-    if (lo < a.base) lo = a.base;   // positions before the launch are complete
-    if (hi <= lo) return true;
+    // thread i takes step t + i / 12 (and every T / 12 steps after), window
+    // (i % 12) / 4, every fourth producer from i % 4
+    constexpr int kPer = 4 * (K + 1);
     const int64_t four_n = 4 * a.N, span = 4 * n_c, ceff = (a.N + n_c - 1) / n_c;
-    const int64_t r0 = lo - a.base, r1 = hi - 1 - a.base;
-    const int64_t L0 = (r0 / four_n) * ceff + (r0 % four_n) / span;
-    const int64_t L1 = (r1 / four_n) * ceff + (r1 % four_n) / span;
     const uint64_t deadline = global_ns() + a.wait_ns;
-    for (int64_t L = L0 + m; L <= L1; L += 4) {
-        const uint64_t* f = a.prog + (L % ceff);
-        const uint64_t need = (uint64_t)(L / ceff) + 1;
-        for (uint32_t n = 1; ld_relaxed_u64(f) < need; ++n) {
-            if ((n & 15u) == 0) {
-                if (ld_volatile_i32(a.status) != DEV_OK) return false;
-                if (global_ns() > deadline) {
-                    atomicCAS(a.status, DEV_OK, DEV_TIMEOUT);
-                    return false;
+    const int jw = (threadIdx.x % kPer) >> 2, m = threadIdx.x & 3;
+    const int64_t back = (int64_t)(K - jw) * a.ll + (int64_t)jw * (a.ll - a.sl);
+    for (int64_t o = threadIdx.x / kPer; o < kr; o += blockDim.x / kPer) {
+        const int64_t q0 = a.base + 4 * ((t + o) * a.N + j0);
+        int64_t lo = q0 - back - 32;
+        const int64_t hi = q0 + 4 * (int64_t)nc - back;
+        if (lo < a.base) lo = a.base;   // positions before the launch are complete
+        if (hi <= lo) continue;
+        const int64_t r0 = lo - a.base, r1 = hi - 1 - a.base;
+        const int64_t L0 = (r0 / four_n) * ceff + (r0 % four_n) / span;
+        const int64_t L1 = (r1 / four_n) * ceff + (r1 % four_n) / span;
+        for (int64_t L = L0 + m; L <= L1; L += 4) {
+            const uint64_t* f = a.prog + (L % ceff);
+            const uint64_t need = (uint64_t)(L / ceff) + 1;
+            for (uint32_t n = 1; ld_relaxed_u64(f) < need; ++n) {
+                if ((n & 15u) == 0) {
+                    if (ld_volatile_i32(a.status) != DEV_OK) return false;
+                    if (global_ns() > deadline) {
+                        atomicCAS(a.status, DEV_OK, DEV_TIMEOUT);
+                        return false;
+                    }
                 }
             }
+            (void)ld_acquire_u64(f);
         }
-        (void)ld_acquire_u64(f);
     }
     return true;
 }
@@ -585,8 +593,10 @@ __global__ void __launch_bounds__(T, 1) lfg_resident_kernel(LfgArgs a, int64_t n
     uint32_t sP = slot_add(a.base_slot, (uint32_t)(4 * min(j0, a.N)), a.R);
     for (int64_t t = 0; t < a.n_steps; ++t) {
         const bool last = t == a.n_steps - 1;
-        if (a.prog) {
-            if (nc > 0 && !dataflow_wait<K>(a, t, j0, nc, n_c)) s_df_fail = 1;
+        if (a.prog && t % kr == 0) {
+            // the round's kr steps read only earlier rounds
+            const int64_t krr = min(kr, a.n_steps - t);
+            if (nc > 0 && !dataflow_wait<K>(a, t, krr, j0, nc, n_c)) s_df_fail = 1;
             __syncthreads();
             if (s_df_fail) return;
         }
@@ -652,9 +662,12 @@ __global__ void __launch_bounds__(T, 1) lfg_resident_kernel(LfgArgs a, int64_t n
         }
         sP = slot_add(sP, step_slots, a.R);
         if (a.prog) {
-            // publish: every ring store of this CTA's step is done
-            __syncthreads();
-            if (threadIdx.x == 0 && arrive_here) st_release_u64(a.prog + blockIdx.x, (uint64_t)t + 1);
+            // publish at the round's end: every ring store of its steps is done
+            if ((t + 1) % kr == 0 || last) {
+                __syncthreads();
+                if (threadIdx.x == 0 && arrive_here)
+                    st_release_u64(a.prog + blockIdx.x, (uint64_t)t + 1);
+            }
         } else if (!last && (t + 1) % kr == 0 &&
                    !grid_barrier(a, (uint64_t)gridDim.x * (uint64_t)((t + 1) / kr), arrive_here)) {
             return;
@@ -911,12 +924,12 @@ static int launch(Handle* h, LfgArgs& a, int k, cudaStream_t st, int64_t* G_out)
 // v.  Returns 1 (and launches) when it applies, 0 when the caller must use the
 // general kernel, or an error.
 // Resident kernel synchronisation: per-CTA dataflow waits (order 2 on the
-// exact ring) instead of the grid barrier, when every round is one step
-// (8N > width).  Same GB300: 11.36 against 11.90 us per step at 1e6
-// oscillators, 7.75 against 8.08 at 6e5.  Where a round holds several steps
-// the barrier is paid once a round while a dataflow wait comes every step
-// (1e5: 3.36 against 1.88 ms per 1000 steps), so those launches keep the
-// barrier.
+// exact ring) instead of the grid barrier where every round is one step (8N >
+// width).  Same GB300: 11.36 against 11.90 us per step at 1e6 oscillators,
+// 7.75 against 8.08 at 6e5.  Where a round holds several steps the barrier
+// stays: even waiting once a round, the dataflow polls cost more than the
+// barrier there (1e5: 2.07 against 1.89 ms per 1000 steps; 1e4: 1.72 against
+// 1.55; equal at 5e5).
 constexpr bool kResDataflow = true;
 
 template <int K, int T>
