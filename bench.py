@@ -366,16 +366,7 @@ def run_gpu(args, rank, world, dist):
         "vs_baseline": None,
         "dtype": "f32+u32",
         "data": "synthetic (seeded oscillators; equilibrium start)",
-        "config": {"workload": WORKLOAD,
-                   "batched": {"systems": BATCH_SYSTEMS, "oscillators": extras["batched_osc"],
-                               "steps": BATCH_STEPS},
-                   "adjoint": {"n": ADJ_N, "steps": ADJ_STEPS, "checkpoint_every": ADJ_CKPT,
-                               "noise": "regenerated from checkpoints"},
-                   "large": {"n": LARGE_N, "steps": LARGE_STEPS, "params": LARGE_PARAMS,
-                             "timed": "once per generator after the steps, outside the step"},
-                   "n_oscillators": N_OSC, "ld_steps": LD_STEPS, "fill_numbers": FILL_N,
-                   "params": PARAMS, "l2": "flushed (256 MiB write) before every part",
-                   "parallelism": f"replicas x{world} (independent seeds, no collective)"},
+        "config": bench_config(world, extras["batched_osc"]),
         "clocks": clk,
         "gpu_launches": gpu_launches(parts, args.steps, extras["batched_tune"]),
         "batched_tune": extras["batched_tune"],
@@ -393,6 +384,19 @@ def run_gpu(args, rank, world, dist):
     roof.update(head)
     line["per_generator"] = head
     return line
+
+
+def bench_config(world, batched_osc):
+    """The workload's description, the same for both arms."""
+    return {"workload": WORKLOAD,
+            "batched": {"systems": BATCH_SYSTEMS, "oscillators": batched_osc, "steps": BATCH_STEPS},
+            "adjoint": {"n": ADJ_N, "steps": ADJ_STEPS, "checkpoint_every": ADJ_CKPT,
+                        "noise": "regenerated from checkpoints"},
+            "large": {"n": LARGE_N, "steps": LARGE_STEPS, "params": LARGE_PARAMS,
+                      "timed": "once per generator after the steps, outside the step"},
+            "n_oscillators": N_OSC, "ld_steps": LD_STEPS, "fill_numbers": FILL_N,
+            "params": PARAMS, "l2": "flushed (256 MiB write) before every part",
+            "parallelism": f"replicas x{world} (independent seeds, no collective)"}
 
 
 def headline(per_part):
@@ -825,7 +829,9 @@ def cpu_baseline(parts, part_ms, steps):
 
 def run_reference(args, world):
     """The oracle on the host cores, timed like our arm: W untimed and K timed
-    steps, each a bounded sample of the workload extrapolated per unit."""
+    steps, each a bounded sample of the workload; value is the rate of the
+    samples extrapolated per unit to the whole step, ms_per_step the measured
+    wall time of a timed (sample) step."""
     scale = 0.5
     workers = os.cpu_count() or 1
     pool = oracle_pool(workers)
@@ -840,19 +846,21 @@ def run_reference(args, world):
     finally:
         if pool:
             pool.shutdown()
-    ms_per_step = 1e3 * statistics.mean(secs)
-    value = _step_osc_steps(_step_units()) / (ms_per_step / 1e3)
+    full_step_ms = 1e3 * statistics.mean(secs)
+    value = _step_osc_steps(_step_units()) / (full_step_ms / 1e3)
+    batched_osc = sum(sp["n"] for sp in W.batched_systems(BATCH_SYSTEMS, seed=1234))
     return {
         "impl": "reference",
         "metric": "oscillator-steps/s (fused LD+RNG, all generators, whole hot path)",
         "value": value, "unit": "oscillator-steps/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+u32",
         "data": "synthetic (seeded oscillators; equilibrium start)",
-        "config": {"workload": WORKLOAD, "timed_wall_s": wall},
+        "config": bench_config(world, batched_osc),
         "cpu_baseline": {"value": value, "unit": "oscillator-steps/s", "cores": workers,
                          "cpu": host_cpu(), "kind": "oracle",
-                         "sample": _sample_text(scale, workers)},
+                         "sample": _sample_text(scale, workers),
+                         "full_step_ms_extrapolated": full_step_ms},
         "e2e": {"value": value, "unit": "oscillator-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

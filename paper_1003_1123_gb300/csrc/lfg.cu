@@ -28,19 +28,30 @@
 // with W <= k D, so no position of a round reads another, and W <= R - k ll,
 // so no position of a round overwrites (slot p - R) a value this or a later
 // round still reads (p - k ll at the farthest).  The persistent cooperative
-// grid computes a round at once and rounds are separated by a grid barrier.
-// For the fused Langevin step a round also holds at most one step (W <= 4N),
-// so each oscillator is updated at most once per round.  This is the paper's
-// one-step-per-launch scheme (Sec. III.C) made exact for any N: the leap turns
-// its race condition ll - sl > 4N into k (ll - sl) >= W.
+// grid computes a round at once.  For the fused Langevin step a round also
+// holds at most one step (W <= 4N), so each oscillator is updated at most
+// once per round.  This is the paper's one-step-per-launch scheme (Sec.
+// III.C) made exact for any N: the leap turns its race condition ll - sl > 4N
+// into k (ll - sl) >= W.
+//
+// Between rounds.  With order 2 on the exact ring (R = 2(ll + D) + r, r <
+// 32) each CTA waits only for the CTAs that computed what its next share
+// reads: the readers of the value a store overwrites (position q - R) are the
+// positions q - back_j - r, i.e. the producers of the lag windows the same
+// positions read, so waiting for the owners of [q_lo - back_j - 32, q_hi -
+// back_j) covers both read after write and write after read (and, in the
+// fused step, the owners of the oscillators' previous step cover their x, v).
+// Each CTA publishes its completed rounds in a counter of its own
+// (st.release / ld.acquire).  Other launches (order 1 or 4, and resident
+// launches with several steps a round) keep a grid barrier: an arrival
+// counter.  Every wait is polled under a %globaltimer bound; a wait that runs
+// out records GBRNG_ETIMEOUT and every CTA returns.
 //
 // Within a round a warp owns blocks of 128 consecutive positions (32
 // oscillator-steps): lane l reads positions 32i + l of each lag window
-// (coalesced), the new values go back to the ring the same way, and a per-warp
-// shared-memory buffer hands lane l positions 4l..4l+3.  A block none of whose
-// windows wraps around the ring addresses each window with one pointer.  The
-// grid barrier is an arrival counter polled under a %globaltimer bound; a wait
-// that runs out records GBRNG_ETIMEOUT and every CTA returns.
+// (coalesced, one pointer per window through the mirror), the new values go
+// back to the ring the same way, and a per-warp shared-memory buffer hands
+// lane l positions 4l..4l+3.
 #include <algorithm>
 #include <atomic>
 
