@@ -193,9 +193,13 @@ __device__ __forceinline__ float sqrt_pos(float y)
     return r;
 }
 
-// sin and cos of (pi/2) x for x = 4u in [0, 4): r = x - rint(x) is exact,
-// theta = (pi/2) r in [-pi/4, pi/4], sin = r S(r^2), cos = C(r^2), then the
-// quadrant q = rint(x) rotates the pair by q quarter turns.
+// Two evaluations of sin and cos of (pi/2) x for x = 4u in (0, 4); each
+// generator uses one of them in every kernel (the per-generator choice below),
+// so all kernels of one generator produce the same normals bit for bit.
+//
+// Quadrant form: r = x - rint(x) is exact, theta = (pi/2) r in [-pi/4, pi/4],
+// sin = r S(r^2), cos = C(r^2), then the quadrant q = rint(x) rotates the pair
+// by q quarter turns (integer selects and sign flips).
 __device__ __forceinline__ void sincos_quarter(float x, float& s, float& c)
 {
     const float qf = rintf(x);
@@ -215,48 +219,112 @@ __device__ __forceinline__ void sincos_quarter(float x, float& s, float& c)
     c = ((q + 1) & 2) ? -co : co;
 }
 
-// sin and cos of 2 pi u for u in [0, 1) (x = 4u is exact).
-__device__ __forceinline__ void sincos2pi(float u, float& s, float& c)
+// Half-turn form, with no integer work: n = rint(x / 2) in {0, 1, 2} (x / 2
+// added to 1.5 * 2^23, where the addition's round-to-nearest drops the
+// fraction, and the constant taken off again), y = x - 2n in [-1, 1] (exact:
+// either x itself or a difference within a factor of two), the sign (-1)^n =
+// (2n - 4) n + 1 (exact for those n), and sin(pi x / 2) = (-1)^n sin(pi y / 2),
+// cos(pi x / 2) = (-1)^n cos(pi y / 2).  With z = y^2: cos(pi y / 2) =
+// (1 - z)(1 + z Q1(z)), the factor 1 - z rounded once so that the zeros at
+// y = +-1 keep their relative accuracy; sin(pi y / 2) = y c0 + y z P1(z), the
+// head y c0 added in the last FMA.  Fewer instructions and no ALU-pipe work,
+// but longer dependent FMA chains: faster where a scheduler holds enough warps
+// to cover them (Ran2 and Lagged Fibonacci kernels), slower in the Hybrid
+// Taus pair kernel at about four warps a scheduler.
+struct HalfTurn {
+    float sgn, y, z, f1;
+};
+
+__device__ __forceinline__ HalfTurn half_turn(float x)
 {
-    sincos_quarter(__fmul_rn(4.0f, u), s, c);
+    const float nf = __fsub_rn(__fmaf_rn(x, 0.5f, 0x1.8p+23f), 0x1.8p+23f);
+    HalfTurn h;
+    h.y = __fmaf_rn(nf, -2.0f, x);
+    h.sgn = __fmaf_rn(__fmaf_rn(nf, 2.0f, -4.0f), nf, 1.0f);
+    h.z = __fmul_rn(h.y, h.y);
+    h.f1 = __fmaf_rn(-h.y, h.y, 1.0f);
+    return h;
 }
 
-// Box-Muller pair from two uniforms in (0, 1).
+__device__ __forceinline__ float cos_half(const HalfTurn& h)
+{
+    const float z = h.z;
+    const float q = __fmaf_rn(__fmaf_rn(__fmaf_rn(kCosQ1[3], z, kCosQ1[2]), z, kCosQ1[1]), z, kCosQ1[0]);
+    return __fmaf_rn(__fmul_rn(h.f1, z), q, h.f1);
+}
+
+__device__ __forceinline__ float sin_half(const HalfTurn& h)
+{
+    const float z = h.z;
+    const float p = __fmaf_rn(
+        __fmaf_rn(__fmaf_rn(__fmaf_rn(kSinP1[4], z, kSinP1[3]), z, kSinP1[2]), z, kSinP1[1]), z,
+        kSinP1[0]);
+    return __fmaf_rn(h.y, kSinC0, __fmul_rn(__fmul_rn(h.y, z), p));
+}
+
+// Box-Muller from m = -2 ln u1 and x = 4 u2: the pair (rho cos, rho sin) and
+// the cosine branch alone (third normal of a particle-step), rho = sqrt(m).
+// In the half-turn form the sign (-1)^n goes on rho (exact), so each result is
+// still one rounding of rho times the signed cos or sin.
+template <bool HALF>
+__device__ __forceinline__ void box_muller_x(float m2log, float x, float& g1, float& g2)
+{
+    if (HALF) {
+        const HalfTurn h = half_turn(x);
+        const float sr = __fmul_rn(h.sgn, sqrt_pos(m2log));
+        g1 = __fmul_rn(sr, cos_half(h));
+        g2 = __fmul_rn(sr, sin_half(h));
+    } else {
+        const float rho = sqrt_pos(m2log);
+        float s, c;
+        sincos_quarter(x, s, c);
+        g1 = __fmul_rn(rho, c);
+        g2 = __fmul_rn(rho, s);
+    }
+}
+
+template <bool HALF>
+__device__ __forceinline__ float box_muller_cos_x(float m2log, float x)
+{
+    if (HALF) {
+        const HalfTurn h = half_turn(x);
+        return __fmul_rn(__fmul_rn(h.sgn, sqrt_pos(m2log)), cos_half(h));
+    } else {
+        const float rho = sqrt_pos(m2log);
+        float s, c;
+        sincos_quarter(x, s, c);
+        return __fmul_rn(rho, c);
+    }
+}
+
+// The per-generator choice (measured on the fused kernels): half-turn for
+// Ran2 and Lagged Fibonacci, quadrant for Hybrid Taus and the LCG.
+template <int KIND>
+constexpr bool kHalfTurn = KIND == GBRNG_RAN2 || KIND == GBRNG_LAGFIB;
+
+// Ran2's transform from two uniforms in (0, 1) (4u is exact).
 __device__ __forceinline__ void box_muller(float u1, float u2, float& g1, float& g2)
 {
-    const float rho = sqrt_pos(neg2log(u1));
-    float s, c;
-    sincos2pi(u2, s, c);
-    g1 = __fmul_rn(rho, c);
-    g2 = __fmul_rn(rho, s);
+    box_muller_x<kHalfTurn<GBRNG_RAN2>>(neg2log(u1), __fmul_rn(4.0f, u2), g1, g2);
 }
 
-// Only the cosine branch (third normal of a particle-step).
 __device__ __forceinline__ float box_muller_cos(float u1, float u2)
 {
-    const float rho = sqrt_pos(neg2log(u1));
-    float s, c;
-    sincos2pi(u2, s, c);
-    return __fmul_rn(rho, c);
+    return box_muller_cos_x<kHalfTurn<GBRNG_RAN2>>(neg2log(u1), __fmul_rn(4.0f, u2));
 }
 
-// The same two transforms from raw 32-bit draws (u = open01_from_u32), with
-// 4u formed directly from the draw.
+// The transforms from raw 32-bit draws (u = open01_from_u32), with 4u formed
+// directly from the draw, for the generator KIND (Taus, LCG, Lagged Fibonacci).
+template <int KIND>
 __device__ __forceinline__ void box_muller_u32(uint32_t r1, uint32_t r2, float& g1, float& g2)
 {
-    const float rho = sqrt_pos(neg2log(open01_from_u32(r1)));
-    float s, c;
-    sincos_quarter(quarter_turns_from_u32(r2), s, c);
-    g1 = __fmul_rn(rho, c);
-    g2 = __fmul_rn(rho, s);
+    box_muller_x<kHalfTurn<KIND>>(neg2log(open01_from_u32(r1)), quarter_turns_from_u32(r2), g1, g2);
 }
 
+template <int KIND>
 __device__ __forceinline__ float box_muller_cos_u32(uint32_t r1, uint32_t r2)
 {
-    const float rho = sqrt_pos(neg2log(open01_from_u32(r1)));
-    float s, c;
-    sincos_quarter(quarter_turns_from_u32(r2), s, c);
-    return __fmul_rn(rho, c);
+    return box_muller_cos_x<kHalfTurn<KIND>>(neg2log(open01_from_u32(r1)), quarter_turns_from_u32(r2));
 }
 
 // Three normals of one particle-step from four draws of the generator.
@@ -268,8 +336,8 @@ struct TausDraw {
         const uint32_t r2 = taus_next(y);
         const uint32_t r3 = taus_next(y);
         const uint32_t r4 = taus_next(y);
-        box_muller_u32(r1, r2, gx, gy);
-        gz = box_muller_cos_u32(r3, r4);
+        box_muller_u32<GBRNG_TAUS>(r1, r2, gx, gy);
+        gz = box_muller_cos_u32<GBRNG_TAUS>(r3, r4);
     }
 };
 
@@ -281,8 +349,8 @@ struct LcgDraw {
         const uint32_t r2 = lcg_next(x);
         const uint32_t r3 = lcg_next(x);
         const uint32_t r4 = lcg_next(x);
-        box_muller_u32(r1, r2, gx, gy);
-        gz = box_muller_cos_u32(r3, r4);
+        box_muller_u32<GBRNG_LCG>(r1, r2, gx, gy);
+        gz = box_muller_cos_u32<GBRNG_LCG>(r3, r4);
     }
 };
 
