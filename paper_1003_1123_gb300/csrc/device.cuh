@@ -327,6 +327,138 @@ __device__ __forceinline__ float box_muller_cos_u32(uint32_t r1, uint32_t r2)
     return box_muller_cos_x<kHalfTurn<KIND>>(neg2log(open01_from_u32(r1)), quarter_turns_from_u32(r2));
 }
 
+// ------------------------------------------- paired Box-Muller (f32x2 lanes)
+// A particle-step's two transforms (the pair from draws 1, 2 and the cosine
+// branch from draws 3, 4) run side by side in the two lanes of the paired
+// binary32 instructions (FFMA2 / FMUL2 / FADD2: one instruction, two
+// independent correctly rounded operations), halving the floating-point
+// instructions of the transform.  Each lane performs exactly the operations of
+// the scalar functions above, in the same order, so the normals are the same
+// bit for bit; only the integer steps (exponent split, quadrant) and sqrt stay
+// per lane.
+__device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
+
+// -2 ln u in both lanes (neg2log, lane by lane).
+__device__ __forceinline__ float2 neg2log2(float2 u)
+{
+    const int bx = __float_as_int(u.x), by = __float_as_int(u.y);
+    const int ex = (bx - 0x3f2aaaab) >> 23, ey = (by - 0x3f2aaaab) >> 23;
+    const float2 m = make_float2(__int_as_float(bx - (ex << 23)), __int_as_float(by - (ey << 23)));
+    const float2 g = __ffma2_rn(m, splat2(-2.0f), splat2(2.0f));
+    const float2 g2 = __fmul2_rn(g, g);
+    const float2 g4 = __fmul2_rn(g2, g2);
+    const float2 p01 = __ffma2_rn(splat2(kLogG[1]), g, splat2(kLogG[0]));
+    const float2 p23 = __ffma2_rn(splat2(kLogG[3]), g, splat2(kLogG[2]));
+    const float2 p45 = __ffma2_rn(splat2(kLogG[5]), g, splat2(kLogG[4]));
+    const float2 p67 = __ffma2_rn(splat2(kLogG[7]), g, splat2(kLogG[6]));
+    const float2 p03 = __ffma2_rn(p23, g2, p01);
+    const float2 p47 = __ffma2_rn(p67, g2, p45);
+    const float2 p48 = __ffma2_rn(splat2(kLogG[8]), g4, p47);
+    const float2 R = __ffma2_rn(p48, g4, p03);
+    const float2 l2m = __ffma2_rn(g2, R, g);
+    const float2 ef = make_float2((float)ex, (float)ey);
+    return __ffma2_rn(ef, splat2(0x1.05c610p-28f), __ffma2_rn(ef, splat2(-0x1.62e430p+0f), l2m));
+}
+
+// Quadrant-form sin and cos of (pi/2) x in both lanes (sincos_quarter, lane by lane).
+__device__ __forceinline__ void sincos_quarter2(float2 x, float2& s, float2& c)
+{
+    const float qx = rintf(x.x), qy = rintf(x.y);
+    const float2 r = __fadd2_rn(x, make_float2(-qx, -qy));
+    const int q[2] = {(int)qx, (int)qy};
+    const float2 z = __fmul2_rn(r, r);
+    const float2 S = __ffma2_rn(
+        __ffma2_rn(__ffma2_rn(splat2(kSinS[3]), z, splat2(kSinS[2])), z, splat2(kSinS[1])), z,
+        splat2(kSinS[0]));
+    const float2 st = __fmul2_rn(r, S);
+    const float2 z2 = __fmul2_rn(z, z);
+    const float2 c01 = __ffma2_rn(splat2(kCosC[1]), z, splat2(kCosC[0]));
+    const float2 c23 = __ffma2_rn(splat2(kCosC[3]), z, splat2(kCosC[2]));
+    const float2 ct = __ffma2_rn(__ffma2_rn(splat2(kCosC[4]), z2, c23), z2, c01);
+    const float sl[2] = {st.x, st.y}, cl[2] = {ct.x, ct.y};
+    float so[2], co[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const bool swap = q[i] & 1;
+        const float a = swap ? cl[i] : sl[i];
+        const float b = swap ? sl[i] : cl[i];
+        so[i] = (q[i] & 2) ? -a : a;
+        co[i] = ((q[i] + 1) & 2) ? -b : b;
+    }
+    s = make_float2(so[0], so[1]);
+    c = make_float2(co[0], co[1]);
+}
+
+// Half-turn reduction and cosine in both lanes (half_turn, cos_half, lane by lane).
+struct HalfTurn2 {
+    float2 sgn, y, z, f1;
+};
+
+__device__ __forceinline__ HalfTurn2 half_turn2(float2 x)
+{
+    const float2 nf = __fadd2_rn(__ffma2_rn(x, splat2(0.5f), splat2(0x1.8p+23f)), splat2(-0x1.8p+23f));
+    HalfTurn2 h;
+    h.y = __ffma2_rn(nf, splat2(-2.0f), x);
+    h.sgn = __ffma2_rn(__ffma2_rn(nf, splat2(2.0f), splat2(-4.0f)), nf, splat2(1.0f));
+    h.z = __fmul2_rn(h.y, h.y);
+    h.f1 = __ffma2_rn(make_float2(-h.y.x, -h.y.y), h.y, splat2(1.0f));
+    return h;
+}
+
+__device__ __forceinline__ float2 cos_half2(const HalfTurn2& h)
+{
+    const float2 z = h.z;
+    const float2 q = __ffma2_rn(
+        __ffma2_rn(__ffma2_rn(splat2(kCosQ1[3]), z, splat2(kCosQ1[2])), z, splat2(kCosQ1[1])), z,
+        splat2(kCosQ1[0]));
+    return __ffma2_rn(__fmul2_rn(h.f1, z), q, h.f1);
+}
+
+// The three normals from m = (-2 ln u1, -2 ln u3) and x = (4 u2, 4 u4):
+// g0 = rho1 cos(2 pi u2), g1 = rho1 sin(2 pi u2), g2 = rho3 cos(2 pi u4).
+template <bool HALF>
+__device__ __forceinline__ void box_muller3_x(float2 m2log, float2 x, float& g0, float& g1,
+                                              float& g2)
+{
+    const float2 rho = make_float2(sqrt_pos(m2log.x), sqrt_pos(m2log.y));
+    if (HALF) {
+        const HalfTurn2 h = half_turn2(x);
+        const float2 sr = __fmul2_rn(h.sgn, rho);
+        const float2 g = __fmul2_rn(sr, cos_half2(h));
+        g0 = g.x;
+        g2 = g.y;
+        g1 = __fmul_rn(sr.x, sin_half(HalfTurn{h.sgn.x, h.y.x, h.z.x, h.f1.x}));
+    } else {
+        float2 s, c;
+        sincos_quarter2(x, s, c);
+        const float2 g = __fmul2_rn(rho, c);
+        g0 = g.x;
+        g2 = g.y;
+        g1 = __fmul_rn(rho.x, s.x);
+    }
+}
+
+// Four raw 32-bit draws of the generator KIND -> three normals.
+template <int KIND>
+__device__ __forceinline__ void box_muller3_u32(uint32_t r1, uint32_t r2, uint32_t r3, uint32_t r4,
+                                                float& g0, float& g1, float& g2)
+{
+    // u lane by lane: neg2log2 reads its input's bit patterns, and a lane
+    // taken from a paired result as integer bits measured wrong
+    const float2 u = make_float2(open01_from_u32(r1), open01_from_u32(r3));
+    const float2 x = __ffma2_rn(splat2(4.0f), make_float2(mant_from_u32(r2), mant_from_u32(r4)),
+                                splat2(-0x1.fffffep+1f));
+    box_muller3_x<kHalfTurn<KIND>>(neg2log2(u), x, g0, g1, g2);
+}
+
+// Ran2's four uniforms -> three normals.
+__device__ __forceinline__ void box_muller3(float u1, float u2, float u3, float u4, float& g0,
+                                            float& g1, float& g2)
+{
+    box_muller3_x<kHalfTurn<GBRNG_RAN2>>(neg2log2(make_float2(u1, u3)),
+                                         __fmul2_rn(splat2(4.0f), make_float2(u2, u4)), g0, g1, g2);
+}
+
 // Three normals of one particle-step from four draws of the generator.
 struct TausDraw {
     uint4 y;
@@ -336,8 +468,7 @@ struct TausDraw {
         const uint32_t r2 = taus_next(y);
         const uint32_t r3 = taus_next(y);
         const uint32_t r4 = taus_next(y);
-        box_muller_u32<GBRNG_TAUS>(r1, r2, gx, gy);
-        gz = box_muller_cos_u32<GBRNG_TAUS>(r3, r4);
+        box_muller3_u32<GBRNG_TAUS>(r1, r2, r3, r4, gx, gy, gz);
     }
 };
 
@@ -349,8 +480,7 @@ struct LcgDraw {
         const uint32_t r2 = lcg_next(x);
         const uint32_t r3 = lcg_next(x);
         const uint32_t r4 = lcg_next(x);
-        box_muller_u32<GBRNG_LCG>(r1, r2, gx, gy);
-        gz = box_muller_cos_u32<GBRNG_LCG>(r3, r4);
+        box_muller3_u32<GBRNG_LCG>(r1, r2, r3, r4, gx, gy, gz);
     }
 };
 
@@ -370,8 +500,7 @@ struct Ran2Draw {
         const float u2 = u01_from_ran2(next());
         const float u3 = u01_from_ran2(next());
         const float u4 = u01_from_ran2(next());
-        box_muller(u1, u2, gx, gy);
-        gz = box_muller_cos(u3, u4);
+        box_muller3(u1, u2, u3, u4, gx, gy, gz);
     }
 };
 

@@ -291,8 +291,7 @@ __device__ __forceinline__ void walk_blocks(const LfgArgs& a, uint32_t s_first, 
 // gx, gy from the first pair, gz from the cosine branch of the second).
 __device__ __forceinline__ void normals3(uint4 w, float& g0, float& g1, float& g2)
 {
-    box_muller_u32<GBRNG_LAGFIB>(w.x, w.y, g0, g1);
-    g2 = box_muller_cos_u32<GBRNG_LAGFIB>(w.z, w.w);
+    box_muller3_u32<GBRNG_LAGFIB>(w.x, w.y, w.z, w.w, g0, g1, g2);
 }
 
 // Euler-Maruyama update of one oscillator (x, v in registers), its energy
@@ -717,8 +716,7 @@ __global__ void __launch_bounds__(256) lfg_step_kernel(LfgArgs a, uint32_t sP, f
 #pragma unroll
     for (int r = 0; r < 4; ++r) ring_store(a, slot_add(s, r, a.R), w[r]);
     float g0, g1, g2;
-    box_muller_u32<GBRNG_LAGFIB>(w[0], w[1], g0, g1);
-    g2 = box_muller_cos_u32<GBRNG_LAGFIB>(w[2], w[3]);
+    box_muller3_u32<GBRNG_LAGFIB>(w[0], w[1], w[2], w[3], g0, g1, g2);
     const float Ki = a.Kper ? a.Kper[j] : a.c.K;
     float* xp = a.x + 3 * j;
     float* vp = a.v + 3 * j;

@@ -52,8 +52,7 @@ __global__ void __launch_bounds__(256) step_pt_kernel(StepArgs a)
         const float u2 = u01_from_ran2(ran2_next(r, iv));
         const float u3 = u01_from_ran2(ran2_next(r, iv));
         const float u4 = u01_from_ran2(ran2_next(r, iv));
-        box_muller(u1, u2, g0, g1);
-        g2 = box_muller_cos(u3, u4);
+        box_muller3(u1, u2, u3, u4, g0, g1, g2);
         r2[i] = r.idum;
         r2[S + i] = r.idum2;
         r2[2 * S + i] = r.iy;
