@@ -84,24 +84,49 @@ __global__ void __launch_bounds__(256, KIND == GBRNG_TAUS && K == 1 ? 6 : 1)
                 for (int q = 0; q < 32; ++q) rd[j].tab[q * T + tid] = d.r2[(3 + q) * d.S + i];
             }
         }
-        for (int64_t t0 = 0; t0 < n_steps; t0 += kEnergyBlock) {
-            const int nb = (int)min((int64_t)kEnergyBlock, n_steps - t0);
-            // two oscillators a thread: two steps a loop iteration (4% faster
-            // on 512 uneven systems; one oscillator a thread is slower unrolled)
-#pragma unroll(K == 2 ? 2 : 1)
-            for (int k = 0; k < nb; ++k) {
+        if constexpr (K == 2) {
+            // two oscillators a thread in the lanes of the paired binary32
+            // instructions (lane j = oscillator j, each lane the scalar step),
+            // two steps a loop iteration
+            const float2 cdt = splat2(c.cdt), cva = splat2(c.cva), cs = splat2(c.cs);
+            const float2 nckx = make_float2(-ckx[0], -ckx[1]);
+            float2 X[3] = {make_float2(x0[0], x0[1]), make_float2(x1[0], x1[1]), make_float2(x2[0], x2[1])};
+            float2 V[3] = {make_float2(v0[0], v0[1]), make_float2(v1[0], v1[1]), make_float2(v2[0], v2[1])};
+            EnergySum2 es2;
+            LcgDraw lc[2];
+            for (int64_t t0 = 0; t0 < n_steps; t0 += kEnergyBlock) {
+                const int nb = (int)min((int64_t)kEnergyBlock, n_steps - t0);
+#pragma unroll 2
+                for (int k = 0; k < nb; ++k) {
+                    float2 g[3];
+                    draw3x2<KIND>(td, lc, rd, g);
 #pragma unroll
-                for (int j = 0; j < K; ++j) {
-                    float g0, g1, g2;
-                    if (KIND == GBRNG_TAUS) td[j].normals3(g0, g1, g2); else rd[j].normals3(g0, g1, g2);
-                    em_component(c.cdt, c.cva, ckx[j], c.cs, g0, x0[j], v0[j]);
-                    em_component(c.cdt, c.cva, ckx[j], c.cs, g1, x1[j], v1[j]);
-                    em_component(c.cdt, c.cva, ckx[j], c.cs, g2, x2[j], v2[j]);
-                    es[j].add(x0[j], x1[j], x2[j], v0[j], v1[j], v2[j]);
+                    for (int q = 0; q < 3; ++q) em_component2(cdt, cva, nckx, cs, g[q], X[q], V[q]);
+                    es2.add(X, V);
                 }
+                es2.flush();
             }
+            x0[0] = X[0].x, x0[1] = X[0].y, x1[0] = X[1].x, x1[1] = X[1].y, x2[0] = X[2].x, x2[1] = X[2].y;
+            v0[0] = V[0].x, v0[1] = V[0].y, v1[0] = V[1].x, v1[1] = V[1].y, v2[0] = V[2].x, v2[1] = V[2].y;
 #pragma unroll
-            for (int j = 0; j < K; ++j) es[j].flush();
+            for (int j = 0; j < 2; ++j) es[j].X = es2.X[j], es[j].V = es2.V[j];
+        } else {
+            for (int64_t t0 = 0; t0 < n_steps; t0 += kEnergyBlock) {
+                const int nb = (int)min((int64_t)kEnergyBlock, n_steps - t0);
+                for (int k = 0; k < nb; ++k) {
+#pragma unroll
+                    for (int j = 0; j < K; ++j) {
+                        float g0, g1, g2;
+                        if (KIND == GBRNG_TAUS) td[j].normals3(g0, g1, g2); else rd[j].normals3(g0, g1, g2);
+                        em_component(c.cdt, c.cva, ckx[j], c.cs, g0, x0[j], v0[j]);
+                        em_component(c.cdt, c.cva, ckx[j], c.cs, g1, x1[j], v1[j]);
+                        em_component(c.cdt, c.cva, ckx[j], c.cs, g2, x2[j], v2[j]);
+                        es[j].add(x0[j], x1[j], x2[j], v0[j], v1[j], v2[j]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < K; ++j) es[j].flush();
+            }
         }
         double acc[4] = {0, 0, 0, 0};
 #pragma unroll

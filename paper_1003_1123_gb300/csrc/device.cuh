@@ -459,6 +459,76 @@ __device__ __forceinline__ void box_muller3(float u1, float u2, float u3, float 
                                          __fmul2_rn(splat2(4.0f), make_float2(u2, u4)), g0, g1, g2);
 }
 
+// Half-turn sine in both lanes (sin_half, lane by lane).
+__device__ __forceinline__ float2 sin_half2(const HalfTurn2& h)
+{
+    const float2 z = h.z;
+    const float2 p = __ffma2_rn(
+        __ffma2_rn(__ffma2_rn(__ffma2_rn(splat2(kSinP1[4]), z, splat2(kSinP1[3])), z, splat2(kSinP1[2])),
+                   z, splat2(kSinP1[1])),
+        z, splat2(kSinP1[0]));
+    return __ffma2_rn(h.y, splat2(kSinC0), __fmul2_rn(__fmul2_rn(h.y, z), p));
+}
+
+// Two oscillators side by side (lane j = oscillator j): the pair (rho cos,
+// rho sin) and the cosine branch, each lane the scalar box_muller_x /
+// box_muller_cos_x.
+template <bool HALF>
+__device__ __forceinline__ void box_muller_pair2(float2 m2log, float2 x, float2& gc, float2& gs)
+{
+    const float2 rho = make_float2(sqrt_pos(m2log.x), sqrt_pos(m2log.y));
+    if (HALF) {
+        const HalfTurn2 h = half_turn2(x);
+        const float2 sr = __fmul2_rn(h.sgn, rho);
+        gc = __fmul2_rn(sr, cos_half2(h));
+        gs = __fmul2_rn(sr, sin_half2(h));
+    } else {
+        float2 s, c;
+        sincos_quarter2(x, s, c);
+        gc = __fmul2_rn(rho, c);
+        gs = __fmul2_rn(rho, s);
+    }
+}
+
+template <bool HALF>
+__device__ __forceinline__ float2 box_muller_cos2(float2 m2log, float2 x)
+{
+    const float2 rho = make_float2(sqrt_pos(m2log.x), sqrt_pos(m2log.y));
+    if (HALF) {
+        const HalfTurn2 h = half_turn2(x);
+        return __fmul2_rn(__fmul2_rn(h.sgn, rho), cos_half2(h));
+    } else {
+        float2 s, c;
+        sincos_quarter2(x, s, c);
+        return __fmul2_rn(rho, c);
+    }
+}
+
+// Three normals of a particle-step for each of two oscillators from their four
+// raw draws r[j][0..3] (generator KIND): g[k] = (normal k of oscillator 0,
+// normal k of oscillator 1).
+template <int KIND>
+__device__ __forceinline__ void normals3x2_u32(const uint32_t (&r)[2][4], float2 (&g)[3])
+{
+    const float2 ua = make_float2(open01_from_u32(r[0][0]), open01_from_u32(r[1][0]));
+    const float2 ub = make_float2(open01_from_u32(r[0][2]), open01_from_u32(r[1][2]));
+    const float2 xa = __ffma2_rn(splat2(4.0f), make_float2(mant_from_u32(r[0][1]), mant_from_u32(r[1][1])),
+                                 splat2(-0x1.fffffep+1f));
+    const float2 xb = __ffma2_rn(splat2(4.0f), make_float2(mant_from_u32(r[0][3]), mant_from_u32(r[1][3])),
+                                 splat2(-0x1.fffffep+1f));
+    box_muller_pair2<kHalfTurn<KIND>>(neg2log2(ua), xa, g[0], g[1]);
+    g[2] = box_muller_cos2<kHalfTurn<KIND>>(neg2log2(ub), xb);
+}
+
+// The same from Ran2's uniforms u[j][0..3].
+__device__ __forceinline__ void normals3x2_ran2(const float (&u)[2][4], float2 (&g)[3])
+{
+    const float2 xa = __fmul2_rn(splat2(4.0f), make_float2(u[0][1], u[1][1]));
+    const float2 xb = __fmul2_rn(splat2(4.0f), make_float2(u[0][3], u[1][3]));
+    box_muller_pair2<kHalfTurn<GBRNG_RAN2>>(neg2log2(make_float2(u[0][0], u[1][0])), xa, g[0], g[1]);
+    g[2] = box_muller_cos2<kHalfTurn<GBRNG_RAN2>>(neg2log2(make_float2(u[0][2], u[1][2])), xb);
+}
+
 // Three normals of one particle-step from four draws of the generator.
 struct TausDraw {
     uint4 y;
@@ -504,6 +574,31 @@ struct Ran2Draw {
     }
 };
 
+// Three normals of a particle-step for each of two oscillators with their own
+// generators (lane j = oscillator j); each generator draws its four numbers
+// in order, as in draw3.
+template <int KIND>
+__device__ __forceinline__ void draw3x2(TausDraw (&td)[2], LcgDraw (&lc)[2], Ran2Draw (&rd)[2],
+                                        float2 (&g)[3])
+{
+    if (KIND == GBRNG_RAN2) {
+        float u[2][4];
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) u[j][q] = u01_from_ran2(rd[j].next());
+        normals3x2_ran2(u, g);
+    } else {
+        uint32_t r[2][4];
+#pragma unroll
+        for (int j = 0; j < 2; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                r[j][q] = KIND == GBRNG_TAUS ? taus_next(td[j].y) : lcg_next(lc[j].x);
+        normals3x2_u32<KIND>(r, g);
+    }
+}
+
 // Three normals of one particle-step from the per-thread generator KIND.
 template <int KIND>
 __device__ __forceinline__ void draw3(TausDraw& td, LcgDraw& lc, Ran2Draw& rd, float& g0, float& g1,
@@ -525,6 +620,17 @@ __device__ __forceinline__ void em_component(float cdt, float cva, float ckx, fl
     const float t = __fmaf_rn(-ckx, x, __fmul_rn(cs, g));
     const float vn = __fmaf_rn(cva, v, t);
     x = __fmaf_rn(cdt, v, x);
+    v = vn;
+}
+
+// Two oscillators' components side by side (lane j = oscillator j), each lane
+// em_component; nckx = -(ckm K_j).
+__device__ __forceinline__ void em_component2(float2 cdt, float2 cva, float2 nckx, float2 cs, float2 g,
+                                              float2& x, float2& v)
+{
+    const float2 t = __ffma2_rn(nckx, x, __fmul2_rn(cs, g));
+    const float2 vn = __ffma2_rn(cva, v, t);
+    x = __ffma2_rn(cdt, v, x);
     v = vn;
 }
 
@@ -579,6 +685,32 @@ struct EnergySum {
     __device__ __forceinline__ double value(float hK, float hm) const
     {
         return (double)hK * X.value() + (double)hm * V.value();
+    }
+};
+
+// EnergySum of two oscillators, the block sums of |x|^2 and |v|^2 in the two
+// lanes (norm2 and the block addition lane by lane).
+struct EnergySum2 {
+    Kahan X[2], V[2];
+    float2 bx = {0.f, 0.f}, bv = {0.f, 0.f};
+    __device__ __forceinline__ static float2 norm2x2(const float2 (&a)[3])
+    {
+        return __ffma2_rn(a[2], a[2], __ffma2_rn(a[1], a[1], __fmul2_rn(a[0], a[0])));
+    }
+    __device__ __forceinline__ void add(const float2 (&x)[3], const float2 (&v)[3])
+    {
+        bx = __fadd2_rn(bx, norm2x2(x));
+        bv = __fadd2_rn(bv, norm2x2(v));
+    }
+    __device__ __forceinline__ void flush()
+    {
+        X[0].add(bx.x), X[1].add(bx.y);
+        V[0].add(bv.x), V[1].add(bv.y);
+        bx = bv = make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ double value(int j, float hK, float hm) const
+    {
+        return (double)hK * X[j].value() + (double)hm * V[j].value();
     }
 };
 

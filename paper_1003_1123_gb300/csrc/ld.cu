@@ -129,56 +129,63 @@ __global__ void __launch_bounds__(32) ld_pair_kernel(LdArgs a, int64_t n_pairs)
     const int64_t W = (int64_t)gridDim.x * blockDim.x;
     const LdCoef c = a.c;
     double acc[4] = {0, 0, 0, 0};
+    const float2 cdt = splat2(c.cdt), cva = splat2(c.cva), cs = splat2(c.cs);
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n_pairs; p += W) {
         int64_t idx[2];
         bool live[2];
-        float x0[2], x1[2], x2[2], v0[2], v1[2], v2[2], ckx[2], hK[2];
+        // lane j of every pair below is oscillator 2p + j
+        float2 X[3], V[3], nckx;
+        float hK[2];
         TausDraw td[2];
         LcgDraw lc[2];
         Ran2Draw rd[2];
-        EnergySum es[2];
+        EnergySum2 es;
+        float xs[2][3], vs[2][3], ck[2];
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             idx[j] = 2 * p + j;
             live[j] = idx[j] < a.n;
             const int64_t i = live[j] ? idx[j] : 2 * p;   // a dead second lane shadows the first
             const float Ki = a.Kper ? a.Kper[i] : c.K;
-            ckx[j] = __fmul_rn(c.ckm, Ki);
+            ck[j] = -__fmul_rn(c.ckm, Ki);
             hK[j] = 0.5f * Ki;
-            x0[j] = a.x[3 * i], x1[j] = a.x[3 * i + 1], x2[j] = a.x[3 * i + 2];
-            v0[j] = a.v[3 * i], v1[j] = a.v[3 * i + 1], v2[j] = a.v[3 * i + 2];
+#pragma unroll
+            for (int q = 0; q < 3; ++q) xs[j][q] = a.x[3 * i + q], vs[j][q] = a.v[3 * i + q];
             if (KIND == GBRNG_TAUS) td[j].y = a.taus[i];
             else lc[j].x = a.lcg[i];
+        }
+        nckx = make_float2(ck[0], ck[1]);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            X[q] = make_float2(xs[0][q], xs[1][q]);
+            V[q] = make_float2(vs[0][q], vs[1][q]);
         }
         for (int64_t t0 = 0; t0 < a.n_steps; t0 += kEnergyBlock) {
             const int nb = (int)min((int64_t)kEnergyBlock, a.n_steps - t0);
 #pragma unroll 2
             for (int k = 0; k < nb; ++k) {
+                float2 g[3];
+                draw3x2<KIND>(td, lc, rd, g);
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    float g0, g1, g2;
-                    draw3<KIND>(td[j], lc[j], rd[j], g0, g1, g2);
-                    em_component(c.cdt, c.cva, ckx[j], c.cs, g0, x0[j], v0[j]);
-                    em_component(c.cdt, c.cva, ckx[j], c.cs, g1, x1[j], v1[j]);
-                    em_component(c.cdt, c.cva, ckx[j], c.cs, g2, x2[j], v2[j]);
-                    es[j].add(x0[j], x1[j], x2[j], v0[j], v1[j], v2[j]);
-                }
+                for (int q = 0; q < 3; ++q) em_component2(cdt, cva, nckx, cs, g[q], X[q], V[q]);
+                es.add(X, V);
             }
-#pragma unroll
-            for (int j = 0; j < 2; ++j) es[j].flush();
+            es.flush();
         }
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             if (!live[j]) continue;
             const int64_t i = idx[j];
-            a.x[3 * i] = x0[j], a.x[3 * i + 1] = x1[j], a.x[3 * i + 2] = x2[j];
-            a.v[3 * i] = v0[j], a.v[3 * i + 1] = v1[j], a.v[3 * i + 2] = v2[j];
+            const float x0 = j ? X[0].y : X[0].x, x1 = j ? X[1].y : X[1].x, x2 = j ? X[2].y : X[2].x;
+            const float v0 = j ? V[0].y : V[0].x, v1 = j ? V[1].y : V[1].x, v2 = j ? V[2].y : V[2].x;
+            a.x[3 * i] = x0, a.x[3 * i + 1] = x1, a.x[3 * i + 2] = x2;
+            a.v[3 * i] = v0, a.v[3 * i + 1] = v1, a.v[3 * i + 2] = v2;
             if (KIND == GBRNG_TAUS) a.taus[i] = td[j].y;
             else a.lcg[i] = lc[j].x;
-            acc[0] += (double)x0[j] * x0[j] + (double)x1[j] * x1[j] + (double)x2[j] * x2[j];
-            acc[1] += (double)v0[j] * v0[j] + (double)v1[j] * v1[j] + (double)v2[j] * v2[j];
-            acc[2] += (double)x0[j] * v0[j] + (double)x1[j] * v1[j] + (double)x2[j] * v2[j];
-            acc[3] += es[j].value(hK[j], c.hm);
+            acc[0] += (double)x0 * x0 + (double)x1 * x1 + (double)x2 * x2;
+            acc[1] += (double)v0 * v0 + (double)v1 * v1 + (double)v2 * v2;
+            acc[2] += (double)x0 * v0 + (double)x1 * v1 + (double)x2 * v2;
+            acc[3] += es.value(j, hK[j], c.hm);
         }
     }
     if (a.partials) {
