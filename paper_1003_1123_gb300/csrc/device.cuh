@@ -193,44 +193,15 @@ __device__ __forceinline__ float sqrt_pos(float y)
     return r;
 }
 
-// Two evaluations of sin and cos of (pi/2) x for x = 4u in (0, 4); each
-// generator uses one of them in every kernel (the per-generator choice below),
-// so all kernels of one generator produce the same normals bit for bit.
-//
-// Quadrant form: r = x - rint(x) is exact, theta = (pi/2) r in [-pi/4, pi/4],
-// sin = r S(r^2), cos = C(r^2), then the quadrant q = rint(x) rotates the pair
-// by q quarter turns (integer selects and sign flips).
-__device__ __forceinline__ void sincos_quarter(float x, float& s, float& c)
-{
-    const float qf = rintf(x);
-    const float r = __fsub_rn(x, qf);
-    const int q = (int)qf;
-    const float z = __fmul_rn(r, r);
-    const float S = __fmaf_rn(__fmaf_rn(__fmaf_rn(kSinS[3], z, kSinS[2]), z, kSinS[1]), z, kSinS[0]);
-    const float st = __fmul_rn(r, S);
-    const float z2 = __fmul_rn(z, z);
-    const float c01 = __fmaf_rn(kCosC[1], z, kCosC[0]);
-    const float c23 = __fmaf_rn(kCosC[3], z, kCosC[2]);
-    const float ct = __fmaf_rn(__fmaf_rn(kCosC[4], z2, c23), z2, c01);
-    const bool swap = q & 1;
-    const float so = swap ? ct : st;
-    const float co = swap ? st : ct;
-    s = (q & 2) ? -so : so;
-    c = ((q + 1) & 2) ? -co : co;
-}
-
-// Half-turn form, with no integer work: n = rint(x / 2) in {0, 1, 2} (x / 2
-// added to 1.5 * 2^23, where the addition's round-to-nearest drops the
-// fraction, and the constant taken off again), y = x - 2n in [-1, 1] (exact:
-// either x itself or a difference within a factor of two), the sign (-1)^n =
-// (2n - 4) n + 1 (exact for those n), and sin(pi x / 2) = (-1)^n sin(pi y / 2),
-// cos(pi x / 2) = (-1)^n cos(pi y / 2).  With z = y^2: cos(pi y / 2) =
-// (1 - z)(1 + z Q1(z)), the factor 1 - z rounded once so that the zeros at
-// y = +-1 keep their relative accuracy; sin(pi y / 2) = y c0 + y z P1(z), the
-// head y c0 added in the last FMA.  Fewer instructions and no ALU-pipe work,
-// but longer dependent FMA chains: faster where a scheduler holds enough warps
-// to cover them (Ran2 and Lagged Fibonacci kernels), slower in the Hybrid
-// Taus pair kernel at about four warps a scheduler.
+// sin and cos of (pi/2) x for x = 4u in (0, 4), with no integer work: n =
+// rint(x / 2) in {0, 1, 2} (x / 2 added to 1.5 * 2^23, where the addition's
+// round-to-nearest drops the fraction, and the constant taken off again),
+// y = x - 2n in [-1, 1] (exact: either x itself or a difference within a
+// factor of two), the sign (-1)^n = (2n - 4) n + 1 (exact for those n), and
+// sin(pi x / 2) = (-1)^n sin(pi y / 2), cos(pi x / 2) = (-1)^n cos(pi y / 2).
+// With z = y^2: cos(pi y / 2) = (1 - z)(1 + z Q1(z)), the factor 1 - z
+// rounded once so that the zeros at y = +-1 keep their relative accuracy;
+// sin(pi y / 2) = y c0 + y z P1(z), the head y c0 added in the last FMA.
 struct HalfTurn {
     float sgn, y, z, f1;
 };
@@ -264,81 +235,60 @@ __device__ __forceinline__ float sin_half(const HalfTurn& h)
 
 // Box-Muller from m = -2 ln u1 and x = 4 u2: the pair (rho cos, rho sin) and
 // the cosine branch alone (third normal of a particle-step), rho = sqrt(m).
-// In the half-turn form the sign (-1)^n goes on rho (exact), so each result is
-// still one rounding of rho times the signed cos or sin.
-template <bool HALF>
+// The sign (-1)^n goes on rho (exact), so each result is one rounding of rho
+// times the signed cos or sin.
 __device__ __forceinline__ void box_muller_x(float m2log, float x, float& g1, float& g2)
 {
-    if (HALF) {
-        const HalfTurn h = half_turn(x);
-        const float sr = __fmul_rn(h.sgn, sqrt_pos(m2log));
-        g1 = __fmul_rn(sr, cos_half(h));
-        g2 = __fmul_rn(sr, sin_half(h));
-    } else {
-        const float rho = sqrt_pos(m2log);
-        float s, c;
-        sincos_quarter(x, s, c);
-        g1 = __fmul_rn(rho, c);
-        g2 = __fmul_rn(rho, s);
-    }
+    const HalfTurn h = half_turn(x);
+    const float sr = __fmul_rn(h.sgn, sqrt_pos(m2log));
+    g1 = __fmul_rn(sr, cos_half(h));
+    g2 = __fmul_rn(sr, sin_half(h));
 }
 
-template <bool HALF>
 __device__ __forceinline__ float box_muller_cos_x(float m2log, float x)
 {
-    if (HALF) {
-        const HalfTurn h = half_turn(x);
-        return __fmul_rn(__fmul_rn(h.sgn, sqrt_pos(m2log)), cos_half(h));
-    } else {
-        const float rho = sqrt_pos(m2log);
-        float s, c;
-        sincos_quarter(x, s, c);
-        return __fmul_rn(rho, c);
-    }
+    const HalfTurn h = half_turn(x);
+    return __fmul_rn(__fmul_rn(h.sgn, sqrt_pos(m2log)), cos_half(h));
 }
 
-// The per-generator choice (measured on the fused kernels): half-turn for
-// Ran2 and Lagged Fibonacci, quadrant for Hybrid Taus and the LCG.
-template <int KIND>
-constexpr bool kHalfTurn = KIND == GBRNG_RAN2 || KIND == GBRNG_LAGFIB;
-
-// Ran2's transform from two uniforms in (0, 1) (4u is exact).
+// From two uniforms in (0, 1) (Ran2; 4u is exact).
 __device__ __forceinline__ void box_muller(float u1, float u2, float& g1, float& g2)
 {
-    box_muller_x<kHalfTurn<GBRNG_RAN2>>(neg2log(u1), __fmul_rn(4.0f, u2), g1, g2);
+    box_muller_x(neg2log(u1), __fmul_rn(4.0f, u2), g1, g2);
 }
 
 __device__ __forceinline__ float box_muller_cos(float u1, float u2)
 {
-    return box_muller_cos_x<kHalfTurn<GBRNG_RAN2>>(neg2log(u1), __fmul_rn(4.0f, u2));
+    return box_muller_cos_x(neg2log(u1), __fmul_rn(4.0f, u2));
 }
 
-// The transforms from raw 32-bit draws (u = open01_from_u32), with 4u formed
-// directly from the draw, for the generator KIND (Taus, LCG, Lagged Fibonacci).
-template <int KIND>
+// From raw 32-bit draws (u = open01_from_u32), with 4u formed directly from
+// the draw (Hybrid Taus, the LCG, Lagged Fibonacci).
 __device__ __forceinline__ void box_muller_u32(uint32_t r1, uint32_t r2, float& g1, float& g2)
 {
-    box_muller_x<kHalfTurn<KIND>>(neg2log(open01_from_u32(r1)), quarter_turns_from_u32(r2), g1, g2);
+    box_muller_x(neg2log(open01_from_u32(r1)), quarter_turns_from_u32(r2), g1, g2);
 }
 
-template <int KIND>
 __device__ __forceinline__ float box_muller_cos_u32(uint32_t r1, uint32_t r2)
 {
-    return box_muller_cos_x<kHalfTurn<KIND>>(neg2log(open01_from_u32(r1)), quarter_turns_from_u32(r2));
+    return box_muller_cos_x(neg2log(open01_from_u32(r1)), quarter_turns_from_u32(r2));
 }
 
 // ------------------------------------------- paired Box-Muller (f32x2 lanes)
-// A particle-step's two transforms (the pair from draws 1, 2 and the cosine
-// branch from draws 3, 4) run side by side in the two lanes of the paired
-// binary32 instructions (FFMA2 / FMUL2 / FADD2: one instruction, two
-// independent correctly rounded operations), halving the floating-point
-// instructions of the transform.  Each lane performs exactly the operations of
-// the scalar functions above, in the same order, so the normals are the same
-// bit for bit; only the integer steps (exponent split, quadrant) and sqrt stay
-// per lane.
+// Two transforms side by side in the two lanes of the paired binary32
+// instructions (FFMA2 / FMUL2 / FADD2: one instruction, two independent
+// correctly rounded operations), halving the floating-point instructions.
+// Each lane performs exactly the operations of the scalar functions above, in
+// the same order, so the normals are the same bit for bit; only the integer
+// exponent split and sqrt stay per lane.  The lanes hold either a
+// particle-step's two transforms (the pair from draws 1, 2 and the cosine
+// branch from draws 3, 4) or the same transform of two oscillators.
 __device__ __forceinline__ float2 splat2(float a) { return make_float2(a, a); }
 
-// -2 ln u in both lanes (neg2log, lane by lane).
+// -2 ln u in both lanes (neg2log, lane by lane).  u must not come straight
+// from a paired instruction: reading such a lane's bit pattern for the
+// exponent split measured wrong in the first lane, so callers form u lane by
+// lane.
 __device__ __forceinline__ float2 neg2log2(float2 u)
 {
     const int bx = __float_as_int(u.x), by = __float_as_int(u.y);
@@ -360,36 +310,7 @@ __device__ __forceinline__ float2 neg2log2(float2 u)
     return __ffma2_rn(ef, splat2(0x1.05c610p-28f), __ffma2_rn(ef, splat2(-0x1.62e430p+0f), l2m));
 }
 
-// Quadrant-form sin and cos of (pi/2) x in both lanes (sincos_quarter, lane by lane).
-__device__ __forceinline__ void sincos_quarter2(float2 x, float2& s, float2& c)
-{
-    const float qx = rintf(x.x), qy = rintf(x.y);
-    const float2 r = __fadd2_rn(x, make_float2(-qx, -qy));
-    const int q[2] = {(int)qx, (int)qy};
-    const float2 z = __fmul2_rn(r, r);
-    const float2 S = __ffma2_rn(
-        __ffma2_rn(__ffma2_rn(splat2(kSinS[3]), z, splat2(kSinS[2])), z, splat2(kSinS[1])), z,
-        splat2(kSinS[0]));
-    const float2 st = __fmul2_rn(r, S);
-    const float2 z2 = __fmul2_rn(z, z);
-    const float2 c01 = __ffma2_rn(splat2(kCosC[1]), z, splat2(kCosC[0]));
-    const float2 c23 = __ffma2_rn(splat2(kCosC[3]), z, splat2(kCosC[2]));
-    const float2 ct = __ffma2_rn(__ffma2_rn(splat2(kCosC[4]), z2, c23), z2, c01);
-    const float sl[2] = {st.x, st.y}, cl[2] = {ct.x, ct.y};
-    float so[2], co[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const bool swap = q[i] & 1;
-        const float a = swap ? cl[i] : sl[i];
-        const float b = swap ? sl[i] : cl[i];
-        so[i] = (q[i] & 2) ? -a : a;
-        co[i] = ((q[i] + 1) & 2) ? -b : b;
-    }
-    s = make_float2(so[0], so[1]);
-    c = make_float2(co[0], co[1]);
-}
-
-// Half-turn reduction and cosine in both lanes (half_turn, cos_half, lane by lane).
+// half_turn, cos_half and sin_half in both lanes.
 struct HalfTurn2 {
     float2 sgn, y, z, f1;
 };
@@ -414,52 +335,6 @@ __device__ __forceinline__ float2 cos_half2(const HalfTurn2& h)
     return __ffma2_rn(__fmul2_rn(h.f1, z), q, h.f1);
 }
 
-// The three normals from m = (-2 ln u1, -2 ln u3) and x = (4 u2, 4 u4):
-// g0 = rho1 cos(2 pi u2), g1 = rho1 sin(2 pi u2), g2 = rho3 cos(2 pi u4).
-template <bool HALF>
-__device__ __forceinline__ void box_muller3_x(float2 m2log, float2 x, float& g0, float& g1,
-                                              float& g2)
-{
-    const float2 rho = make_float2(sqrt_pos(m2log.x), sqrt_pos(m2log.y));
-    if (HALF) {
-        const HalfTurn2 h = half_turn2(x);
-        const float2 sr = __fmul2_rn(h.sgn, rho);
-        const float2 g = __fmul2_rn(sr, cos_half2(h));
-        g0 = g.x;
-        g2 = g.y;
-        g1 = __fmul_rn(sr.x, sin_half(HalfTurn{h.sgn.x, h.y.x, h.z.x, h.f1.x}));
-    } else {
-        float2 s, c;
-        sincos_quarter2(x, s, c);
-        const float2 g = __fmul2_rn(rho, c);
-        g0 = g.x;
-        g2 = g.y;
-        g1 = __fmul_rn(rho.x, s.x);
-    }
-}
-
-// Four raw 32-bit draws of the generator KIND -> three normals.
-template <int KIND>
-__device__ __forceinline__ void box_muller3_u32(uint32_t r1, uint32_t r2, uint32_t r3, uint32_t r4,
-                                                float& g0, float& g1, float& g2)
-{
-    // u lane by lane: neg2log2 reads its input's bit patterns, and a lane
-    // taken from a paired result as integer bits measured wrong
-    const float2 u = make_float2(open01_from_u32(r1), open01_from_u32(r3));
-    const float2 x = __ffma2_rn(splat2(4.0f), make_float2(mant_from_u32(r2), mant_from_u32(r4)),
-                                splat2(-0x1.fffffep+1f));
-    box_muller3_x<kHalfTurn<KIND>>(neg2log2(u), x, g0, g1, g2);
-}
-
-// Ran2's four uniforms -> three normals.
-__device__ __forceinline__ void box_muller3(float u1, float u2, float u3, float u4, float& g0,
-                                            float& g1, float& g2)
-{
-    box_muller3_x<kHalfTurn<GBRNG_RAN2>>(neg2log2(make_float2(u1, u3)),
-                                         __fmul2_rn(splat2(4.0f), make_float2(u2, u4)), g0, g1, g2);
-}
-
-// Half-turn sine in both lanes (sin_half, lane by lane).
 __device__ __forceinline__ float2 sin_half2(const HalfTurn2& h)
 {
     const float2 z = h.z;
@@ -470,44 +345,59 @@ __device__ __forceinline__ float2 sin_half2(const HalfTurn2& h)
     return __ffma2_rn(h.y, splat2(kSinC0), __fmul2_rn(__fmul2_rn(h.y, z), p));
 }
 
+// One particle-step's three normals from m = (-2 ln u1, -2 ln u3) and
+// x = (4 u2, 4 u4): g0 = rho1 cos(2 pi u2), g1 = rho1 sin(2 pi u2),
+// g2 = rho3 cos(2 pi u4).
+__device__ __forceinline__ void box_muller3_x(float2 m2log, float2 x, float& g0, float& g1, float& g2)
+{
+    const float2 rho = make_float2(sqrt_pos(m2log.x), sqrt_pos(m2log.y));
+    const HalfTurn2 h = half_turn2(x);
+    const float2 sr = __fmul2_rn(h.sgn, rho);
+    const float2 g = __fmul2_rn(sr, cos_half2(h));
+    g0 = g.x;
+    g2 = g.y;
+    g1 = __fmul_rn(sr.x, sin_half(HalfTurn{h.sgn.x, h.y.x, h.z.x, h.f1.x}));
+}
+
+// Four raw 32-bit draws -> three normals.
+__device__ __forceinline__ void box_muller3_u32(uint32_t r1, uint32_t r2, uint32_t r3, uint32_t r4,
+                                                float& g0, float& g1, float& g2)
+{
+    const float2 u = make_float2(open01_from_u32(r1), open01_from_u32(r3));
+    const float2 x = __ffma2_rn(splat2(4.0f), make_float2(mant_from_u32(r2), mant_from_u32(r4)),
+                                splat2(-0x1.fffffep+1f));
+    box_muller3_x(neg2log2(u), x, g0, g1, g2);
+}
+
+// Ran2's four uniforms -> three normals.
+__device__ __forceinline__ void box_muller3(float u1, float u2, float u3, float u4, float& g0,
+                                            float& g1, float& g2)
+{
+    box_muller3_x(neg2log2(make_float2(u1, u3)), __fmul2_rn(splat2(4.0f), make_float2(u2, u4)), g0,
+                  g1, g2);
+}
+
 // Two oscillators side by side (lane j = oscillator j): the pair (rho cos,
-// rho sin) and the cosine branch, each lane the scalar box_muller_x /
-// box_muller_cos_x.
-template <bool HALF>
+// rho sin) and the cosine branch.
 __device__ __forceinline__ void box_muller_pair2(float2 m2log, float2 x, float2& gc, float2& gs)
 {
     const float2 rho = make_float2(sqrt_pos(m2log.x), sqrt_pos(m2log.y));
-    if (HALF) {
-        const HalfTurn2 h = half_turn2(x);
-        const float2 sr = __fmul2_rn(h.sgn, rho);
-        gc = __fmul2_rn(sr, cos_half2(h));
-        gs = __fmul2_rn(sr, sin_half2(h));
-    } else {
-        float2 s, c;
-        sincos_quarter2(x, s, c);
-        gc = __fmul2_rn(rho, c);
-        gs = __fmul2_rn(rho, s);
-    }
+    const HalfTurn2 h = half_turn2(x);
+    const float2 sr = __fmul2_rn(h.sgn, rho);
+    gc = __fmul2_rn(sr, cos_half2(h));
+    gs = __fmul2_rn(sr, sin_half2(h));
 }
 
-template <bool HALF>
 __device__ __forceinline__ float2 box_muller_cos2(float2 m2log, float2 x)
 {
     const float2 rho = make_float2(sqrt_pos(m2log.x), sqrt_pos(m2log.y));
-    if (HALF) {
-        const HalfTurn2 h = half_turn2(x);
-        return __fmul2_rn(__fmul2_rn(h.sgn, rho), cos_half2(h));
-    } else {
-        float2 s, c;
-        sincos_quarter2(x, s, c);
-        return __fmul2_rn(rho, c);
-    }
+    const HalfTurn2 h = half_turn2(x);
+    return __fmul2_rn(__fmul2_rn(h.sgn, rho), cos_half2(h));
 }
 
 // Three normals of a particle-step for each of two oscillators from their four
-// raw draws r[j][0..3] (generator KIND): g[k] = (normal k of oscillator 0,
-// normal k of oscillator 1).
-template <int KIND>
+// raw draws r[j][0..3]: g[k] = (normal k of oscillator 0, normal k of
+// oscillator 1).
 __device__ __forceinline__ void normals3x2_u32(const uint32_t (&r)[2][4], float2 (&g)[3])
 {
     const float2 ua = make_float2(open01_from_u32(r[0][0]), open01_from_u32(r[1][0]));
@@ -516,8 +406,8 @@ __device__ __forceinline__ void normals3x2_u32(const uint32_t (&r)[2][4], float2
                                  splat2(-0x1.fffffep+1f));
     const float2 xb = __ffma2_rn(splat2(4.0f), make_float2(mant_from_u32(r[0][3]), mant_from_u32(r[1][3])),
                                  splat2(-0x1.fffffep+1f));
-    box_muller_pair2<kHalfTurn<KIND>>(neg2log2(ua), xa, g[0], g[1]);
-    g[2] = box_muller_cos2<kHalfTurn<KIND>>(neg2log2(ub), xb);
+    box_muller_pair2(neg2log2(ua), xa, g[0], g[1]);
+    g[2] = box_muller_cos2(neg2log2(ub), xb);
 }
 
 // The same from Ran2's uniforms u[j][0..3].
@@ -525,8 +415,8 @@ __device__ __forceinline__ void normals3x2_ran2(const float (&u)[2][4], float2 (
 {
     const float2 xa = __fmul2_rn(splat2(4.0f), make_float2(u[0][1], u[1][1]));
     const float2 xb = __fmul2_rn(splat2(4.0f), make_float2(u[0][3], u[1][3]));
-    box_muller_pair2<kHalfTurn<GBRNG_RAN2>>(neg2log2(make_float2(u[0][0], u[1][0])), xa, g[0], g[1]);
-    g[2] = box_muller_cos2<kHalfTurn<GBRNG_RAN2>>(neg2log2(make_float2(u[0][2], u[1][2])), xb);
+    box_muller_pair2(neg2log2(make_float2(u[0][0], u[1][0])), xa, g[0], g[1]);
+    g[2] = box_muller_cos2(neg2log2(make_float2(u[0][2], u[1][2])), xb);
 }
 
 // Three normals of one particle-step from four draws of the generator.
@@ -538,7 +428,7 @@ struct TausDraw {
         const uint32_t r2 = taus_next(y);
         const uint32_t r3 = taus_next(y);
         const uint32_t r4 = taus_next(y);
-        box_muller3_u32<GBRNG_TAUS>(r1, r2, r3, r4, gx, gy, gz);
+        box_muller3_u32(r1, r2, r3, r4, gx, gy, gz);
     }
 };
 
@@ -550,7 +440,7 @@ struct LcgDraw {
         const uint32_t r2 = lcg_next(x);
         const uint32_t r3 = lcg_next(x);
         const uint32_t r4 = lcg_next(x);
-        box_muller3_u32<GBRNG_LCG>(r1, r2, r3, r4, gx, gy, gz);
+        box_muller3_u32(r1, r2, r3, r4, gx, gy, gz);
     }
 };
 
@@ -595,7 +485,7 @@ __device__ __forceinline__ void draw3x2(TausDraw (&td)[2], LcgDraw (&lc)[2], Ran
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 r[j][q] = KIND == GBRNG_TAUS ? taus_next(td[j].y) : lcg_next(lc[j].x);
-        normals3x2_u32<KIND>(r, g);
+        normals3x2_u32(r, g);
     }
 }
 

@@ -21,8 +21,7 @@ __device__ __forceinline__ void emit_word(State& y, int64_t idx, void* out)
         const uint32_t r1 = next_word(y);
         const uint32_t r2 = next_word(y);
         float2 g;
-        constexpr int kind = sizeof(State) == sizeof(uint4) ? GBRNG_TAUS : GBRNG_LCG;
-        box_muller_u32<kind>(r1, r2, g.x, g.y);
+        box_muller_u32(r1, r2, g.x, g.y);
         ((float2*)out)[idx] = g;
     }
 }

@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(128, KIND == GBRNG_LCG ? 7 : 6) ld_pt_kernel(L
 template <int KIND>
 __global__ void __launch_bounds__(32) ld_pair_kernel(LdArgs a, int64_t n_pairs)
 {
+    extern __shared__ int32_t tab[];   // Ran2: [2][32][blockDim.x], one table per lane oscillator
     __shared__ double red[4 * 32];
     const int64_t W = (int64_t)gridDim.x * blockDim.x;
     const LdCoef c = a.c;
@@ -151,8 +152,20 @@ __global__ void __launch_bounds__(32) ld_pair_kernel(LdArgs a, int64_t n_pairs)
             hK[j] = 0.5f * Ki;
 #pragma unroll
             for (int q = 0; q < 3; ++q) xs[j][q] = a.x[3 * i + q], vs[j][q] = a.v[3 * i + q];
-            if (KIND == GBRNG_TAUS) td[j].y = a.taus[i];
-            else lc[j].x = a.lcg[i];
+            if (KIND == GBRNG_TAUS) {
+                td[j].y = a.taus[i];
+            } else if (KIND == GBRNG_LCG) {
+                lc[j].x = a.lcg[i];
+            } else {
+                rd[j].tab = tab + j * 32 * blockDim.x;
+                rd[j].T = blockDim.x;
+                rd[j].tid = threadIdx.x;
+                rd[j].r.idum = a.r2[i];
+                rd[j].r.idum2 = a.r2[a.S + i];
+                rd[j].r.iy = a.r2[2 * a.S + i];
+#pragma unroll 4
+                for (int q = 0; q < 32; ++q) rd[j].tab[q * blockDim.x + threadIdx.x] = a.r2[(3 + q) * a.S + i];
+            }
         }
         nckx = make_float2(ck[0], ck[1]);
 #pragma unroll
@@ -180,8 +193,17 @@ __global__ void __launch_bounds__(32) ld_pair_kernel(LdArgs a, int64_t n_pairs)
             const float v0 = j ? V[0].y : V[0].x, v1 = j ? V[1].y : V[1].x, v2 = j ? V[2].y : V[2].x;
             a.x[3 * i] = x0, a.x[3 * i + 1] = x1, a.x[3 * i + 2] = x2;
             a.v[3 * i] = v0, a.v[3 * i + 1] = v1, a.v[3 * i + 2] = v2;
-            if (KIND == GBRNG_TAUS) a.taus[i] = td[j].y;
-            else a.lcg[i] = lc[j].x;
+            if (KIND == GBRNG_TAUS) {
+                a.taus[i] = td[j].y;
+            } else if (KIND == GBRNG_LCG) {
+                a.lcg[i] = lc[j].x;
+            } else {
+                a.r2[i] = rd[j].r.idum;
+                a.r2[a.S + i] = rd[j].r.idum2;
+                a.r2[2 * a.S + i] = rd[j].r.iy;
+#pragma unroll 4
+                for (int q = 0; q < 32; ++q) a.r2[(3 + q) * a.S + i] = rd[j].tab[q * blockDim.x + threadIdx.x];
+            }
             acc[0] += (double)x0 * x0 + (double)x1 * x1 + (double)x2 * x2;
             acc[1] += (double)v0 * v0 + (double)v1 * v1 + (double)v2 * v2;
             acc[2] += (double)x0 * v0 + (double)x1 * v1 + (double)x2 * v2;
@@ -211,8 +233,9 @@ static int launch_pairs(const ld_system* s, int64_t n_steps, bool want_stats, in
     DevInfo di;
     GB_CHECK(dev_info(h->device, &di));
     const int T = 32;
+    const size_t smem = KIND == GBRNG_RAN2 ? sizeof(int32_t) * 2 * 32 * T : 0;
     int occ = 0;
-    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ld_pair_kernel<KIND>, T, 0));
+    GB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ld_pair_kernel<KIND>, T, smem));
     if (occ < 1) return 0;
     const int64_t pairs = (s->n + 1) / 2, wave = (int64_t)di.sms * occ * T;
     if (pairs < wave) return 0;
@@ -230,7 +253,7 @@ static int launch_pairs(const ld_system* s, int64_t n_steps, bool want_stats, in
     a.lcg = h->lcg;
     a.S = h->n;
     a.partials = want_stats ? h->partials : nullptr;
-    ld_pair_kernel<KIND><<<(unsigned)blocks, T, 0, st>>>(a, pairs);
+    ld_pair_kernel<KIND><<<(unsigned)blocks, T, smem, st>>>(a, pairs);
     GB_CUDA(cudaGetLastError());
     *blocks_out = blocks;
     return 1;
@@ -300,6 +323,8 @@ int ld_run_pt(const ld_system* s, int64_t n_steps, ld_stats* out, cudaStream_t s
         rc = launch_pairs<GBRNG_TAUS>(s, n_steps, want, &blocks, st);
     else if (s->rng->kind == GBRNG_LCG)
         rc = launch_pairs<GBRNG_LCG>(s, n_steps, want, &blocks, st);
+    else if (s->rng->kind == GBRNG_RAN2)
+        rc = launch_pairs<GBRNG_RAN2>(s, n_steps, want, &blocks, st);
     if (rc < 0) return rc;
     if (rc == 1) return finish_stats(s->rng, blocks, n_steps, out, st);
     if (s->rng->kind == GBRNG_TAUS)

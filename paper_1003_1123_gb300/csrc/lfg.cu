@@ -291,7 +291,7 @@ __device__ __forceinline__ void walk_blocks(const LfgArgs& a, uint32_t s_first, 
 // gx, gy from the first pair, gz from the cosine branch of the second).
 __device__ __forceinline__ void normals3(uint4 w, float& g0, float& g1, float& g2)
 {
-    box_muller3_u32<GBRNG_LAGFIB>(w.x, w.y, w.z, w.w, g0, g1, g2);
+    box_muller3_u32(w.x, w.y, w.z, w.w, g0, g1, g2);
 }
 
 // Euler-Maruyama update of one oscillator (x, v in registers), its energy
@@ -404,11 +404,11 @@ __global__ void __launch_bounds__(kLfgThreads, lfg_min_blocks<MODE>()) lfg_kerne
                                    const int i = 4 * lane;
                                    float2 o;
                                    if (i < nval) {
-                                       box_muller_u32<GBRNG_LAGFIB>(w.x, w.y, o.x, o.y);
+                                       box_muller_u32(w.x, w.y, o.x, o.y);
                                        __stcs((float2*)((float*)a.out + u0 + i), o);
                                    }
                                    if (i + 2 < nval) {
-                                       box_muller_u32<GBRNG_LAGFIB>(w.z, w.w, o.x, o.y);
+                                       box_muller_u32(w.z, w.w, o.x, o.y);
                                        __stcs((float2*)((float*)a.out + u0 + i + 2), o);
                                    }
                                } else {
@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(256) lfg_step_kernel(LfgArgs a, uint32_t sP, f
 #pragma unroll
     for (int r = 0; r < 4; ++r) ring_store(a, slot_add(s, r, a.R), w[r]);
     float g0, g1, g2;
-    box_muller3_u32<GBRNG_LAGFIB>(w[0], w[1], w[2], w[3], g0, g1, g2);
+    box_muller3_u32(w[0], w[1], w[2], w[3], g0, g1, g2);
     const float Ki = a.Kper ? a.Kper[j] : a.c.K;
     float* xp = a.x + 3 * j;
     float* vp = a.v + 3 * j;
@@ -774,7 +774,7 @@ __global__ void __launch_bounds__(256) lfg_ou_kernel(LfgArgs a, OuCoef c, float*
             const uint32_t w0 = load_lags<K>(a, s0).value(), w1 = load_lags<K>(a, s1).value();
             ring_store(a, s0, w0);
             ring_store(a, s1, w1);
-            const float g = box_muller_cos_u32<GBRNG_LAGFIB>(w0, w1);
+            const float g = box_muller_cos_u32(w0, w1);
             R[j] = __fmaf_rn(c.cs, g, __fmaf_rn(-c.c1, R[j], R[j]));
         }
         sP = slot_add(sP, step_slots, a.R);

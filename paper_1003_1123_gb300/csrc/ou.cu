@@ -29,11 +29,11 @@ __device__ __forceinline__ float normal1(TausDraw& td, LcgDraw& lc, Ran2Draw& rd
     if (KIND == GBRNG_TAUS) {
         const uint32_t r1 = taus_next(td.y);
         const uint32_t r2 = taus_next(td.y);
-        return box_muller_cos_u32<GBRNG_TAUS>(r1, r2);
+        return box_muller_cos_u32(r1, r2);
     } else if (KIND == GBRNG_LCG) {
         const uint32_t r1 = lcg_next(lc.x);
         const uint32_t r2 = lcg_next(lc.x);
-        return box_muller_cos_u32<GBRNG_LCG>(r1, r2);
+        return box_muller_cos_u32(r1, r2);
     } else {
         const float u1 = u01_from_ran2(rd.next());
         const float u2 = u01_from_ran2(rd.next());

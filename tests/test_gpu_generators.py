@@ -11,9 +11,7 @@ from paper_1003_1123_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 # Box-Muller normals: the library's reduced-range -2 ln u and sqrt are within
-# 1 ulp and its sin/cos of 2 pi u within 1.9 ulp in either form (quadrant for
-# Hybrid Taus and the LCG, half-turn for Ran2 and Lagged Fibonacci;
-# fit_bm_coeffs.py); the oracle
+# 1 ulp and its sin/cos of 2 pi u within 1.9 ulp (fit_bm_coeffs.py); the oracle
 # rounds rho, cos and sin once each from double.  Both sides are within a few
 # ulp of the exact value: |d| <= 2e-6 |g| + 1e-7 leaves a margin of ~4.
 NORMAL_RTOL, NORMAL_ATOL = 2e-6, 1e-7
