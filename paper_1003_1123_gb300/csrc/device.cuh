@@ -395,6 +395,31 @@ __device__ __forceinline__ float2 box_muller_cos2(float2 m2log, float2 x)
     return __fmul2_rn(__fmul2_rn(h.sgn, rho), cos_half2(h));
 }
 
+// Two Box-Muller pairs side by side, from draws (r1, r2) and (r3, r4): a =
+// box_muller_u32(r1, r2), b = box_muller_u32(r3, r4), bit for bit.
+__device__ __forceinline__ void box_muller_2pairs_u32(uint32_t r1, uint32_t r2, uint32_t r3, uint32_t r4,
+                                                      float2& a, float2& b)
+{
+    const float2 u = make_float2(open01_from_u32(r1), open01_from_u32(r3));
+    const float2 x = __ffma2_rn(splat2(4.0f), make_float2(mant_from_u32(r2), mant_from_u32(r4)),
+                                splat2(-0x1.fffffep+1f));
+    float2 gc, gs;
+    box_muller_pair2(neg2log2(u), x, gc, gs);
+    a = make_float2(gc.x, gs.x);
+    b = make_float2(gc.y, gs.y);
+}
+
+// The same from Ran2's uniforms: a = box_muller(u1, u2), b = box_muller(u3, u4).
+__device__ __forceinline__ void box_muller_2pairs(float u1, float u2, float u3, float u4, float2& a,
+                                                  float2& b)
+{
+    float2 gc, gs;
+    box_muller_pair2(neg2log2(make_float2(u1, u3)), __fmul2_rn(splat2(4.0f), make_float2(u2, u4)), gc,
+                     gs);
+    a = make_float2(gc.x, gs.x);
+    b = make_float2(gc.y, gs.y);
+}
+
 // Three normals of a particle-step for each of two oscillators from their four
 // raw draws r[j][0..3]: g[k] = (normal k of oscillator 0, normal k of
 // oscillator 1).

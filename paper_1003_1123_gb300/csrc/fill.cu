@@ -39,10 +39,23 @@ __global__ void __launch_bounds__(256) word_fill_kernel(State* __restrict__ st, 
         int64_t idx = s;
         // four draws in flight per iteration: independent stores, one state chain
         for (; idx + 3 * S < n_items; idx += 4 * S) {
-            emit_word<MODE>(y, idx, out);
-            emit_word<MODE>(y, idx + S, out);
-            emit_word<MODE>(y, idx + 2 * S, out);
-            emit_word<MODE>(y, idx + 3 * S, out);
+            if (MODE == FILL_NORMAL) {
+                // the four pairs two at a time in the paired instructions' lanes
+                uint32_t r[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) r[q] = next_word(y);
+                float2* o = (float2*)out;
+                float2 ga, gb;
+                box_muller_2pairs_u32(r[0], r[1], r[2], r[3], ga, gb);
+                o[idx] = ga, o[idx + S] = gb;
+                box_muller_2pairs_u32(r[4], r[5], r[6], r[7], ga, gb);
+                o[idx + 2 * S] = ga, o[idx + 3 * S] = gb;
+            } else {
+                emit_word<MODE>(y, idx, out);
+                emit_word<MODE>(y, idx + S, out);
+                emit_word<MODE>(y, idx + 2 * S, out);
+                emit_word<MODE>(y, idx + 3 * S, out);
+            }
         }
         for (; idx < n_items; idx += S) emit_word<MODE>(y, idx, out);
         st[s] = y;
@@ -78,10 +91,23 @@ __global__ void __launch_bounds__(128) ran2_fill_kernel(int32_t* __restrict__ st
         int64_t idx = s;
         // four draws a loop iteration: one bound check for four stores
         for (; idx + 3 * S < n_items; idx += 4 * S) {
-            emit(idx);
-            emit(idx + S);
-            emit(idx + 2 * S);
-            emit(idx + 3 * S);
+            if (MODE == FILL_NORMAL) {
+                // the four pairs two at a time in the paired instructions' lanes
+                float u[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) u[q] = u01_from_ran2(ran2_next(r, iv));
+                float2* o = (float2*)out;
+                float2 ga, gb;
+                box_muller_2pairs(u[0], u[1], u[2], u[3], ga, gb);
+                o[idx] = ga, o[idx + S] = gb;
+                box_muller_2pairs(u[4], u[5], u[6], u[7], ga, gb);
+                o[idx + 2 * S] = ga, o[idx + 3 * S] = gb;
+            } else {
+                emit(idx);
+                emit(idx + S);
+                emit(idx + 2 * S);
+                emit(idx + 3 * S);
+            }
         }
         for (; idx < n_items; idx += S) emit(idx);
         st[s] = r.idum;

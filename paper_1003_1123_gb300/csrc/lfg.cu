@@ -401,16 +401,13 @@ __global__ void __launch_bounds__(kLfgThreads, lfg_min_blocks<MODE>()) lfg_kerne
                                const int64_t u0 = U + 128 * b;   // launch offset of the block
                                if (MODE == LFG_NORMAL) {
                                    // positions u0 + 4l .. + 3: pairs (2e, 2e + 1); nval is even
+                                   // (both pairs in the paired instructions' lanes; past
+                                   // nval the values are computed and dropped)
                                    const int i = 4 * lane;
-                                   float2 o;
-                                   if (i < nval) {
-                                       box_muller_u32(w.x, w.y, o.x, o.y);
-                                       __stcs((float2*)((float*)a.out + u0 + i), o);
-                                   }
-                                   if (i + 2 < nval) {
-                                       box_muller_u32(w.z, w.w, o.x, o.y);
-                                       __stcs((float2*)((float*)a.out + u0 + i + 2), o);
-                                   }
+                                   float2 ga, gb;
+                                   box_muller_2pairs_u32(w.x, w.y, w.z, w.w, ga, gb);
+                                   if (i < nval) __stcs((float2*)((float*)a.out + u0 + i), ga);
+                                   if (i + 2 < nval) __stcs((float2*)((float*)a.out + u0 + i + 2), gb);
                                } else {
                                    const uint32_t* bv = bufs[warp];
 #pragma unroll
