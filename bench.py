@@ -92,7 +92,7 @@ LFG_FILL_BYTES_PER_NUMBER = 16
 # capture summarised in profiles/ (same kernel, same launch shape), keyed by
 # part and the batched tuner's (T, K, steps per launch); reported as the
 # roofline's `traffic` only when this run chose that shape.
-NCU_TRAFFIC = {("batched_taus", (64, 2, 0)): 302.803456e6 + 237.171456e6}
+NCU_TRAFFIC = {("batched_taus", (64, 2, 0)): 303.498496e6 + 237.612032e6}
 # ncu's ALU-pipe utilisation (sm__pipe_alu_cycles_active, % of peak sustained
 # active) of each ALU-bound part's kernel, from the captures summarised in
 # profiles/alu_pipe_by_part.md (same kernel and launch shape as the bench;
