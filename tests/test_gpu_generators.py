@@ -104,6 +104,23 @@ def test_normal_within_tolerance(G, kind):
     assert state_payload(G, r)[1] == oracle_state_bytes(g)
 
 
+@pytest.mark.parametrize("kind", ["taus", "ran2"])
+def test_paired_normals_equal_scalar_path(G, kind):
+    """The normal fills evaluate two Box-Muller pairs at a time in the lanes of
+    the paired binary32 instructions inside their four-pair loop and one pair at
+    a time in the loop's tail; each lane performs the scalar operations, so the
+    two paths give the same bits.  Five pairs a stream in one call (pairs 0-3
+    paired, pair 4 scalar) against five one-pair calls (all scalar)."""
+    S = 4096
+    a = G.rng_init(kind, 77, S)
+    b = G.rng_init(kind, 77, S)
+    whole = u32(G.rng_fill_normal(a, 2 * 5 * S)).reshape(5, S, 2)
+    for d in range(5):
+        one = u32(G.rng_fill_normal(b, 2 * S)).reshape(S, 2)
+        assert np.array_equal(whole[d], one), d
+    assert G.rng_get_state(a) == G.rng_get_state(b)
+
+
 @pytest.mark.parametrize("row", list(range(10)))
 def test_lfg_every_table_row(G, row):
     """Every Table I row: several dependency rounds (n >> ll - sl), odd split."""

@@ -287,13 +287,14 @@ def test_lagfib_timeout_reported_without_fault(G):
     assert G.rng_fill_u32(r2, 10**6).numel() == 10**6
 
 
-@pytest.mark.parametrize("path", ["resident", "resident_dataflow", "fill", "ou"])
+@pytest.mark.parametrize("path", ["resident", "resident_dataflow", "fill", "fill_narrow_rounds", "ou"])
 def test_lagfib_timeouts_on_every_cooperative_kernel(G, path):
     """The stall hook (one CTA never arrives at the grid barrier, or never
     publishes its steps to the CTAs that wait on it) ends the resident-state
-    fused kernel in both of its synchronisation modes, the fill rounds and the
-    overdamped run with GBRNG_ETIMEOUT after the wait limit; the context stays
-    usable."""
+    fused kernel in both of its synchronisation modes, the fill rounds (per-CTA
+    waits where a round fills the grid, the grid barrier on Table I row 0's
+    narrow rounds) and the overdamped run with GBRNG_ETIMEOUT after the wait
+    limit; the context stays usable."""
     # 1e6 oscillators: one step a round, so the resident kernel waits per CTA
     n = 10**6 if path == "resident_dataflow" else 10**5
     r = G.rng_init("lagfib", 9, n)
@@ -310,6 +311,8 @@ def test_lagfib_timeouts_on_every_cooperative_kernel(G, path):
                 G.ld_run(s, 100, stats=False)
             elif path == "fill":
                 G.rng_fill_uniform(r, 32 * 10**6)
+            elif path == "fill_narrow_rounds":
+                G.rng_fill_uniform(G.rng_init_lfg(9, 1000, 0), 10**6)
             else:
                 ro = G.rng_init("lagfib", 9, 1000)
                 G.ou_run(G.OuSystem(ro, torch.zeros(1000, dtype=torch.float32, device="cuda")),
