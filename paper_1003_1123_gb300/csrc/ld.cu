@@ -116,12 +116,15 @@ __global__ void __launch_bounds__(128, KIND == GBRNG_LCG ? 7 : 6) ld_pt_kernel(L
     }
 }
 
-// Two oscillators a thread (Hybrid Taus and the LCG): thread g takes the
+// Two oscillators a thread (Hybrid Taus, the LCG, Ran2): thread g takes the
 // adjacent pairs (2p, 2p + 1) for p = g, g + W, ..., and advances both in the
 // same loop, two steps an iteration, so each thread carries two independent
-// generator chains.  One-warp blocks, one full resident wave.  Per oscillator
-// the draws, operations and state are those of ld_pt_kernel, bit for bit;
-// only the order of the final sums over oscillators differs.
+// generator chains, and the two oscillators' floating-point work (transforms,
+// update, energy sums) runs in the two lanes of the paired binary32
+// instructions.  One-warp blocks, one full resident wave; Ran2's two tables in
+// shared-memory columns.  Per oscillator the draws, operations and state are
+// those of ld_pt_kernel, bit for bit; only the order of the final sums over
+// oscillators differs.
 template <int KIND>
 __global__ void __launch_bounds__(32) ld_pair_kernel(LdArgs a, int64_t n_pairs)
 {
@@ -218,13 +221,15 @@ __global__ void __launch_bounds__(32) ld_pair_kernel(LdArgs a, int64_t n_pairs)
     }
 }
 
-// Pair-kernel grid: one full resident wave of one-warp blocks (17 a SM at
-// 1e6 oscillators).  Measured at 1e6 oscillators x 1000 steps: 5.90 ms for
-// Hybrid Taus against 6.13 ms for one oscillator a thread; 64-, 128- and
-// 256-thread blocks 6.06-6.60 ms; a grid trimmed so that every thread gets the
-// same number of pairs (fewer warps a SM) 6.36 ms.  Returns 0 (and launches
-// nothing) when the pairs do not fill one resident wave, where one oscillator
-// a thread spreads better.
+// Pair-kernel grid: one full resident wave of one-warp blocks (16 a SM for
+// Taus, 20 for Ran2 at 1e6 oscillators).  Measured at 1e6 oscillators x 1000
+// steps (scalar arithmetic): 5.90 ms for Hybrid Taus against 6.13 ms for one
+// oscillator a thread; 64-, 128- and 256-thread blocks 6.06-6.60 ms; a grid
+// trimmed so that every thread gets the same number of pairs (fewer warps a
+// SM) 6.36 ms.  With the paired instructions: Taus 4.9 ms, Ran2 6.3 ms (64-
+// thread blocks for Ran2 equal).  Returns 0 (and launches nothing) when the
+// pairs do not fill one resident wave, where one oscillator a thread spreads
+// better.
 template <int KIND>
 static int launch_pairs(const ld_system* s, int64_t n_steps, bool want_stats, int64_t* blocks_out,
                         cudaStream_t st)
