@@ -1003,9 +1003,25 @@ def run_sweep():
                          "portable_state_bytes": G.rng_state_bytes(r),
                          "ms_per_1000": timed(lambda: G.ld_run(s, steps, stats=False))})
         del s, x, r
+    # the overdamped 1-D test of Sec. IV (Eq. 4-5) at the paper's parameters
+    # (k_sp = 0.01 pN/nm, T = 300 K, D = 0.25 nm^2/ns, dt = 1 ps, R0 = 10 nm):
+    # 1000 steps with a record every 100, at the paper's N = 1e4 and at 1e6
+    kT_ou = 1.380649e-2 * 300.0   # pN nm
+    ou_params = dict(k_sp=0.01, xi=kT_ou / 0.25, kT=kT_ou, dt=1e-3)
+    ou = []
+    for n in (10**4, 10**6):
+        for kind in KINDS + ("lcg",):
+            r = G.rng_init(kind, SEED + 2, n)
+            R = torch.full((n,), 10.0, dtype=torch.float32, device="cuda")
+            o = G.OuSystem(r, R, **ou_params)
+            ms = timed(lambda: G.ou_run(o, steps, every=100))
+            ou.append({"n": n, "kind": kind, "ms_per_1000": ms,
+                       "particle_steps_per_s": n * steps / (ms * 1e-3)})
+            del o, R, r
     return {"sweep": "time per 1000 steps vs N (E2), state bytes (E3), RNG share (E4), "
-                     "Table I rows at N = 1000",
-            "params": PARAMS, "rows": rows, "lag_rows": lag_rows, "clocks": clocks.stop()}
+                     "Table I rows at N = 1000, overdamped runs (Sec. IV)",
+            "params": PARAMS, "rows": rows, "lag_rows": lag_rows, "ou_params": ou_params,
+            "ou": ou, "clocks": clocks.stop()}
 
 
 def main():

@@ -41,6 +41,30 @@ __device__ __forceinline__ float normal1(TausDraw& td, LcgDraw& lc, Ran2Draw& rd
     }
 }
 
+// The normals of two consecutive steps (draws of step t, then of step t + 1)
+// in the two lanes of the paired binary32 instructions: each lane is
+// normal1's transform, bit for bit.
+template <int KIND>
+__device__ __forceinline__ float2 normal2(TausDraw& td, LcgDraw& lc, Ran2Draw& rd)
+{
+    if (KIND == GBRNG_RAN2) {
+        const float u1 = u01_from_ran2(rd.next());
+        const float u2 = u01_from_ran2(rd.next());
+        const float u3 = u01_from_ran2(rd.next());
+        const float u4 = u01_from_ran2(rd.next());
+        return box_muller_cos2(neg2log2(make_float2(u1, u3)),
+                               __fmul2_rn(splat2(4.0f), make_float2(u2, u4)));
+    } else {
+        uint32_t r[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) r[q] = KIND == GBRNG_TAUS ? taus_next(td.y) : lcg_next(lc.x);
+        const float2 u = make_float2(open01_from_u32(r[0]), open01_from_u32(r[2]));
+        const float2 x = __ffma2_rn(splat2(4.0f), make_float2(mant_from_u32(r[1]), mant_from_u32(r[3])),
+                                    splat2(-0x1.fffffep+1f));
+        return box_muller_cos2(neg2log2(u), x);
+    }
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(256) ou_pt_kernel(OuArgs a)
 {
@@ -69,7 +93,7 @@ __global__ void __launch_bounds__(256) ou_pt_kernel(OuArgs a)
     float R = live ? a.R[k] : 0.f;
     const float R0 = R;
     int64_t rec = 0, next_rec = 0;
-    for (int64_t t = 0;; ++t) {
+    for (int64_t t = 0;;) {
         if (a.partials && t == next_rec) {
             next_rec += a.every;
             double v[2] = {live ? (double)R : 0.0, live ? (double)R * (double)R0 : 0.0};
@@ -82,8 +106,17 @@ __global__ void __launch_bounds__(256) ou_pt_kernel(OuArgs a)
             ++rec;
         }
         if (t == a.n_steps) break;
-        const float g = normal1<KIND>(td, lc, rd);
-        R = __fmaf_rn(a.c.cs, g, __fmaf_rn(-a.c.c1, R, R));
+        if (t + 1 < a.n_steps && !(a.partials && t + 1 == next_rec)) {
+            // two steps with no record between them
+            const float2 g = normal2<KIND>(td, lc, rd);
+            R = __fmaf_rn(a.c.cs, g.x, __fmaf_rn(-a.c.c1, R, R));
+            R = __fmaf_rn(a.c.cs, g.y, __fmaf_rn(-a.c.c1, R, R));
+            t += 2;
+        } else {
+            const float g = normal1<KIND>(td, lc, rd);
+            R = __fmaf_rn(a.c.cs, g, __fmaf_rn(-a.c.c1, R, R));
+            t += 1;
+        }
     }
     if (!live) return;
     a.R[i] = R;
