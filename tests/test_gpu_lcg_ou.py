@@ -93,6 +93,26 @@ def test_ou_matches_oracle(G, kind):
     assert rel(R.cpu().numpy(), Ro) < 1e-5
 
 
+def test_ou_lagfib_several_steps_a_round(G):
+    """Lagged Fibonacci overdamped run with three steps a round (Table I row 5,
+    2 (ll - sl) = 42068 positions, 2N = 14000): 101 steps with a record every
+    7, so rounds end between records and records fall inside rounds; values,
+    records and the ring match the oracle."""
+    n, steps, every = 7000, 101, 7
+    kw = dict(k_sp=1.5, xi=2.0, kT=1.0, dt=0.01)
+    R0 = np.linspace(-2, 5, n).astype(np.float32)
+    r = G.rng_init_lfg(33, n, lag_row=5)
+    R = torch.from_numpy(R0.copy()).cuda()
+    mean, corr = G.ou_run(G.OuSystem(r, R, **kw), steps, every)
+    g = oracle.Gen("lagfib", 33, n, lag_row=5)
+    Ro = R0.copy()
+    mo, co = oracle.ou_run_f32(g, Ro, oracle.ou_params(**kw), steps, every)
+    assert rel(R.cpu().numpy(), Ro) < 1e-5
+    assert np.allclose(mean, mo, rtol=1e-5, atol=1e-5 * np.abs(Ro).max())
+    assert np.allclose(corr, co, rtol=1e-5, atol=1e-5 * float((R0.astype(float) ** 2).mean()))
+    assert G.parse_state(G.rng_get_state(r))[1] == g.ring_in_order().tobytes()
+
+
 def test_ou_lagfib_rejects_dependent_rounds(G):
     """A step of 2N positions must fit one round: 2N <= 4 (ll - sl) = 4116 on
     row 0 (the order-4 leap), so N = 2100 is refused."""

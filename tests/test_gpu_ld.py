@@ -314,8 +314,10 @@ def test_lagfib_timeouts_on_every_cooperative_kernel(G, path):
             elif path == "fill_narrow_rounds":
                 G.rng_fill_uniform(G.rng_init_lfg(9, 1000, 0), 10**6)
             else:
-                ro = G.rng_init("lagfib", 9, 1000)
-                G.ou_run(G.OuSystem(ro, torch.zeros(1000, dtype=torch.float32, device="cuda")),
+                # 1e6 particles: two steps a round (2 (ll - sl) / 2N), so the
+                # run takes a grid barrier every second step
+                ro = G.rng_init("lagfib", 9, 10**6)
+                G.ou_run(G.OuSystem(ro, torch.zeros(10**6, dtype=torch.float32, device="cuda")),
                          50, 10)
         assert e.value.code == -4
     finally:
