@@ -24,19 +24,35 @@ __host__ __device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64
 // ------------------------------------------------------------- Hybrid Taus
 // One Tausworthe word step (Algorithm 1): b = ((y << S1) ^ y) >> S2,
 // y = ((y & C) << S3) ^ b.
-template <int S1, int S2, int S3, uint32_t C>
+// With MUL the two left shifts are written as multiplies by 2^S (the same
+// bits), which the FMA pipe's integer multiply-add can take off the ALU pipe;
+// used where that measured faster (the two-oscillator fused kernel).
+template <int S>
+__device__ __forceinline__ uint32_t shl_mul(uint32_t y)
+{
+    uint32_t r;
+    asm("mul.lo.u32 %0, %1, %2;" : "=r"(r) : "r"(y), "n"(1u << S));
+    return r;
+}
+
+template <int S1, int S2, int S3, uint32_t C, bool MUL = false>
 __device__ __forceinline__ uint32_t taus_word(uint32_t y)
 {
+    if (MUL) {
+        const uint32_t b = (shl_mul<S1>(y) ^ y) >> S2;
+        return (shl_mul<S3>(y) & (C << S3)) ^ b;
+    }
     const uint32_t b = ((y << S1) ^ y) >> S2;
     return ((y & C) << S3) ^ b;
 }
 
 // Advance the three Tausworthe words and the LCG, return their xor.
+template <bool MUL = false>
 __device__ __forceinline__ uint32_t taus_next(uint4& s)
 {
-    s.x = taus_word<13, 19, 12, 0xFFFFFFFEu>(s.x);
-    s.y = taus_word<2, 25, 4, 0xFFFFFFF8u>(s.y);
-    s.z = taus_word<3, 11, 17, 0xFFFFFFF0u>(s.z);
+    s.x = taus_word<13, 19, 12, 0xFFFFFFFEu, MUL>(s.x);
+    s.y = taus_word<2, 25, 4, 0xFFFFFFF8u, MUL>(s.y);
+    s.z = taus_word<3, 11, 17, 0xFFFFFFF0u, MUL>(s.z);
     s.w = 1664525u * s.w + 1013904223u;
     return s.x ^ s.y ^ s.z ^ s.w;
 }
@@ -492,7 +508,7 @@ struct Ran2Draw {
 // Three normals of a particle-step for each of two oscillators with their own
 // generators (lane j = oscillator j); each generator draws its four numbers
 // in order, as in draw3.
-template <int KIND>
+template <int KIND, bool MUL = false>
 __device__ __forceinline__ void draw3x2(TausDraw (&td)[2], LcgDraw (&lc)[2], Ran2Draw (&rd)[2],
                                         float2 (&g)[3])
 {
@@ -509,7 +525,7 @@ __device__ __forceinline__ void draw3x2(TausDraw (&td)[2], LcgDraw (&lc)[2], Ran
         for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                r[j][q] = KIND == GBRNG_TAUS ? taus_next(td[j].y) : lcg_next(lc[j].x);
+                r[j][q] = KIND == GBRNG_TAUS ? taus_next<MUL>(td[j].y) : lcg_next(lc[j].x);
         normals3x2_u32(r, g);
     }
 }
