@@ -99,11 +99,11 @@ NCU_TRAFFIC = {("batched_taus", (64, 2, 0)): 303.498496e6 + 237.612032e6}
 # 100 steps of the 1e6-oscillator systems, 1000 steps of the adjoint, 2^28
 # fill numbers, the batched graph's replay; the large parts at 1e7
 # oscillators x 10 steps).
-NCU_ALU_PIPE_PCT = {"ld_taus": 66.5, "batched_taus": 69.7, "ld_ran2": 47.7,
+NCU_ALU_PIPE_PCT = {"ld_taus": 69.5, "batched_taus": 69.7, "ld_ran2": 47.7,
                     "adjoint_taus": 60.2, "adjoint_ran2": 42.2,
                     "fill_uniform_taus": 89.1, "fill_normal_taus": 77.8,
                     "fill_uniform_ran2": 65.5, "fill_normal_ran2": 63.3,
-                    "ld_taus_1e8": 55.3, "ld_ran2_1e8": 39.5}
+                    "ld_taus_1e8": 56.0, "ld_ran2_1e8": 39.5}
 
 
 def load_peaks():
